@@ -1,0 +1,327 @@
+"""Throughput of exact negacyclic polynomial multiplication on GB300.
+
+Workload (the headline configuration): independent products c = a * b in
+Z_q[X]/(X^N + 1) with N = 2^16 and q the largest 60-bit prime with
+q = 1 mod 2^17, operands uniform in [0, q), `--batch` products per step
+(default 1024: 1 GiB of operands, larger than L2, so no flush is needed
+between steps).
+
+One step = one pm_polymul call over the batch (forward NTTs of a and b,
+Barrett pointwise product, inverse NTT), timed with CUDA events on its
+stream.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle (the plain C implementation under
+oracle/) on a bounded sample of the same workload on the host cores.
+Multi-GPU: one replica per rank (the products are independent), launched by
+torch.distributed.run; the value is the units of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "negacyclic polymults/sec (N=2^16, 60-bit q) and % of HBM/INT-mul roofline"
+
+
+def mulmods_per_polymul(log2n: int) -> int:
+    """Algorithmic modular products of Eq. 2: 3 NTTs of N/2 log2 N butterflies
+    plus N pointwise products."""
+    n = 1 << log2n
+    return 3 * (n // 2) * log2n + n
+
+
+def rows_kernel_mulmods(log2n: int) -> int:
+    """Modular products done by the row kernel of the split path for one unit:
+    12 forward in-row stages on a and b, the pointwise product and 12 inverse
+    in-row stages."""
+    n = 1 << log2n
+    rows_stages = min(12, log2n)
+    return 2 * rows_stages * (n // 2) + n + rows_stages * (n // 2)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    return rank, ws, local, dist
+
+
+def cpu_baseline(log2n: int, qs, psis, seconds: float = 12.0):
+    """The oracle's scalar-NTT product on the host cores, on a bounded sample
+    of the workload: as many products as fit in about `seconds`."""
+    import oracle
+    from paper_2209_01290_gb300 import inputs
+    cores = os.cpu_count() or 1
+    n = 1 << log2n
+    a, b = inputs.operand_pair(inputs.seed_for(1) + 77, qs, cores, n)
+    a2, b2 = a.reshape(-1, n), b.reshape(-1, n)
+    t0 = time.perf_counter()
+    oracle.polymul_ntt_batch(a2[:1], b2[:1], qs, psis, nthreads=1)  # probe one
+    one = time.perf_counter() - t0
+    per_thread = max(1, int(seconds / max(one, 1e-6)) // 4)
+    units = min(cores * per_thread, cores * 64)
+    reps = max(1, units // a2.shape[0])
+    A = np.concatenate([a2] * reps)[:units]
+    B = np.concatenate([b2] * reps)[:units]
+    t0 = time.perf_counter()
+    oracle.polymul_ntt_batch(A, B, qs, psis, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": "polymuls/s", "cores": cores, "kind": "oracle",
+            "sample": f"{units} products at N=2^{log2n} (oracle textbook-NTT product, "
+                      f"{cores} threads, {dt:.2f} s)"}
+
+
+def run_reference(args):
+    rank, ws, local, dist = _dist()
+    if rank != 0:
+        return 0
+    from paper_2209_01290_gb300 import capi
+    qs, psis = capi.pm_find_params(args.log2n, args.limbs, 60)
+    import oracle
+    from paper_2209_01290_gb300 import inputs
+    cores = os.cpu_count() or 1
+    n = 1 << args.log2n
+    per_step = cores  # one product per core per step
+    a, b = inputs.operand_pair(inputs.seed_for(1), qs, max(1, per_step // args.limbs), n)
+    A, B = a.reshape(-1, n)[:per_step], b.reshape(-1, n)[:per_step]
+    for _ in range(args.warmup):
+        oracle.polymul_ntt_batch(A[:1], B[:1], qs, psis, nthreads=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.polymul_ntt_batch(A, B, qs, psis, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = A.shape[0] * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "polymuls/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"N=2^{args.log2n} negacyclic products, 60-bit q, "
+                               f"{A.shape[0]} products per step (bounded CPU sample)"},
+        "cpu_baseline": {"value": value, "unit": "polymuls/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{A.shape[0]} products per step x {args.steps} steps"},
+        "e2e": {"value": value, "unit": "polymuls/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, ws, local, dist = _dist()
+    if dist is not None:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.cuda.current_device()
+    from paper_2209_01290_gb300 import Plan, capi, inputs
+
+    log2n, n, L = args.log2n, 1 << args.log2n, args.limbs
+    npoly = max(1, args.batch // L)
+    units = npoly * L
+    qs, psis = capi.pm_find_params(log2n, L, 60)
+    plan = Plan(n, qs, psis, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan.reserve(npoly, stream=stream)
+
+    a, b = inputs.operand_pair(inputs.seed_for(1) + 1000 * rank, qs, npoly, n)
+    ha = torch.from_numpy(a.view(np.int64)).pin_memory()
+    hb = torch.from_numpy(b.view(np.int64)).pin_memory()
+    hc = torch.empty_like(ha).pin_memory()
+    with torch.cuda.stream(stream):
+        da = ha.to(dev, non_blocking=True)
+        db = hb.to(dev, non_blocking=True)
+        dc = torch.empty_like(da)
+    stream.synchronize()
+
+    peak_mulmod, peak_imad = capi.pm_measure_peaks(dev)
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        plan.polymul(da, db, out=dc, stream=stream)
+    stream.synchronize()
+
+    # per-step phase events (recorded by the library on `stream`)
+    nphase = 4 if log2n >= 14 else 2
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nphase)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)  # let the sampler attach before the timed region
+    start.record(stream)
+    for k in range(args.steps):
+        capi.pm_plan_set_phase_events(plan.handle, [e.cuda_event for e in ev[k]])
+        plan.polymul(da, db, out=dc, stream=stream)
+    end.record(stream)
+    stream.synchronize()
+    clocks = sampler.stop()
+    capi.pm_plan_set_phase_events(plan.handle, [])
+    torch.cuda.synchronize(dev)
+    elapsed_ms = start.elapsed_time(end)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        dist.barrier()
+    phase_ms = [[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(nphase - 1)]
+                for k in range(args.steps)]
+    avg_phase = [sum(p[i] for p in phase_ms) / args.steps for i in range(nphase - 1)]
+
+    value = ws * units * args.steps / (elapsed_ms * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_steps = max(2, min(5, args.steps))
+    plan.polymul_host(ha, hb, hc, da, db, dc, stream=stream)  # warm
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.polymul_host(ha, hb, hc, da, db, dc, stream=stream)
+    e2e_dt = time.perf_counter() - t0
+    e2e_value = units / (e2e_dt / e2e_steps)
+    if dist is not None:
+        t = torch.tensor([e2e_dt], device=f"cuda:{dev}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_value = ws * units / (float(t.item()) / e2e_steps)
+
+    # ---- roofline: the dominant kernel (rows, or the single fused kernel)
+    if log2n >= 14:
+        dom_idx, dom_name = 1, "k_rows<POLYMUL> (in-row stages + Barrett pointwise)"
+        dom_mulmods = rows_kernel_mulmods(log2n) * units
+    else:
+        dom_idx, dom_name = 0, "fused single-kernel polymul"
+        dom_mulmods = mulmods_per_polymul(log2n) * units
+    dom_ms = avg_phase[dom_idx]
+    achieved = dom_mulmods / (dom_ms * 1e-3)
+    step_mulmod_rate = mulmods_per_polymul(log2n) * units / (elapsed_ms / args.steps * 1e-3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "polymuls/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"N=2^{log2n} negacyclic polymul, q = largest 60-bit prime "
+                               f"= 1 mod 2^{log2n + 1} ({L} limb(s)), {units} independent "
+                               f"products per step, uniform coefficients",
+                   "N": n, "limbs": L, "products_per_step": units,
+                   "operand_bytes_per_step": units * n * 8 * 3,
+                   "l2": "inputs (%.2f GiB) larger than L2, no flush" % (units * n * 16 / 2**30),
+                   "parallelism": f"replicas x{ws}"},
+        "gpu_launches": (3 if log2n >= 14 else 1) * args.steps,
+        "phase_ms": {"col_fwd": avg_phase[0], "rows": avg_phase[1], "col_inv": avg_phase[2]}
+        if log2n >= 14 else {"fused": avg_phase[0]},
+        "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12,
+                     "peak": peak_mulmod / 1e12, "unit": "Tmulmod/s",
+                     "frac": achieved / peak_mulmod, "traffic": None,
+                     "peak_source": "measured register-resident 60-bit Shoup mulmod rate "
+                                    "(pm_measure_peaks, same process)",
+                     "imad_peak_tops": peak_imad / 1e12,
+                     "step_frac": step_mulmod_rate / peak_mulmod,
+                     "mulmods_per_polymul": mulmods_per_polymul(log2n)},
+        "e2e": {"value": e2e_value, "unit": "polymuls/s",
+                "h2d_bytes_per_step": 2 * units * n * 8, "d2h_bytes_per_step": units * n * 8},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(log2n, qs, psis, seconds=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--log2n", type=int, default=16)
+    ap.add_argument("--limbs", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=1024, help="products per step")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

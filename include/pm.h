@@ -1,0 +1,177 @@
+/*
+ * pm.h -- C ABI of the GB300 (sm_103a) negacyclic polynomial multiplication
+ * library: c = a * b in Z_q[X]/(X^N + 1), following arxiv 2209.01290.
+ *
+ * The hot path (Eq. 2 of the paper):
+ *   c = NTT^{GS, psi^-1}_{bo->no, 1/2}( NTT^{CT, psi}_{no->bo}(a) . NTT^{CT, psi}_{no->bo}(b) )
+ * i.e. a merged Cooley-Tukey forward NTT (Algorithm 6), a pointwise product
+ * reduced with the paper's Barrett variant (Algorithm 4), and a merged
+ * Gentleman-Sande inverse NTT (Algorithm 7) with the 1/N scaling folded into
+ * its butterflies as halvings (Sec. III-A).  Many independent products (RNS
+ * limbs x polynomials) run in one launch.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Coefficients are uint64 words.  A batch is laid out [npoly][nlimbs][N],
+ *   contiguous, row-major: unit u = p * nlimbs + l starts at word u * N and
+ *   uses limb l's modulus q_l.
+ * - Inputs must be reduced, 0 <= x < q_l (the REQUIRE of Algorithms 1 and 4).
+ *   The fast path does not check this; pm_check_reduced() does.
+ *   Outputs are always canonical, 0 <= x < q_l.
+ * - "d_" pointers are device pointers (cudaMalloc / torch CUDA tensors) owned
+ *   by the caller, 16-byte aligned.  "h_" pointers are host pointers.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Compute calls are asynchronous on that stream: argument errors
+ *   are returned synchronously; errors from the device surface on the next
+ *   call on the plan or from pm_plan_sync().
+ * - Every call returns a pm_status; on failure pm_last_error() gives a
+ *   human-readable message (thread-local).
+ * - A plan may be used from several host threads on different streams at
+ *   once; destroying it while work is in flight is the caller's error.
+ * - For N >= 2^14, pm_polymul needs [npoly][nlimbs][N] words of device
+ *   scratch.  The plan keeps one scratch area per stream and grows it on
+ *   demand; growing allocates (cudaMalloc, and cudaFree of the old area,
+ *   which synchronises the device).  Call pm_plan_reserve() first when the
+ *   call must not allocate (for example inside CUDA graph capture).
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pm_status {
+    PM_OK = 0,
+    PM_ERR_ARG = -1,         /* null pointer, zero/oversized count, misaligned pointer */
+    PM_ERR_N = -2,           /* N not a power of two in [2, 2^17] */
+    PM_ERR_Q = -3,           /* q not prime, not = 1 mod 2N, or q >= 2^62 */
+    PM_ERR_PSI = -4,         /* psi^N != -1 mod q (not a primitive 2N-th root) */
+    PM_ERR_CUDA = -5,        /* a CUDA runtime call failed (message has the CUDA error) */
+    PM_ERR_OOM = -6,         /* device allocation failed */
+    PM_ERR_TIMEOUT = -7,     /* a bounded device-side wait gave up */
+    PM_ERR_BUDGET = -8,      /* request exceeds the configured device-memory budget */
+    PM_ERR_UNSUPPORTED = -9, /* this GPU cannot run the requested launch shape */
+    PM_ERR_RANGE = -10       /* pm_check_reduced found a coefficient >= q */
+} pm_status;
+
+/* Opaque plan: owns the device twiddle tables, Barrett/Shoup constants and
+ * the launch choices for one (N, {q_l}, {psi_l}). */
+typedef struct pm_plan pm_plan;
+
+/* Largest moduli for a given N (setup of Sec. III-A: q prime with 2N | q-1,
+ * psi a primitive 2N-th root of unity).
+ *   log2n   : log2 N, 1..17
+ *   nlimbs  : number of moduli wanted (1..1024)
+ *   qbits   : moduli are < 2^qbits, 3 <= qbits <= 62 (Algorithm 4 needs
+ *             len(q) <= 64 - 2)
+ *   q_out   : host[nlimbs], the nlimbs largest primes q < 2^qbits with
+ *             q = 1 mod 2N, descending
+ *   psi_out : host[nlimbs] or NULL; psi_l = x^((q_l-1)/2N) for the first
+ *             x = 2, 3, ... with psi_l^N = q_l - 1
+ * Returns PM_ERR_Q if fewer than nlimbs such primes exist. */
+pm_status pm_find_params(uint32_t log2n, uint32_t nlimbs, uint32_t qbits,
+                         uint64_t *q_out, uint64_t *psi_out);
+
+/* Create a plan (twiddle-table setup, Sec. III-A and Sec. VI-A: tables are
+ * precomputed on the host and kept on the device).
+ *   out     : receives the plan
+ *   log2n   : log2 N, 1..17
+ *   nlimbs  : number of RNS limbs L (1..1024)
+ *   q       : host[nlimbs] moduli; each prime, = 1 mod 2N, 3 < q < 2^62
+ *   psi     : host[nlimbs] primitive 2N-th roots, or NULL to derive them
+ *             with the rule of pm_find_params
+ *   device  : CUDA device ordinal the plan lives on
+ * The plan builds, per limb, Psi_br[i] = psi^br(i) and
+ * Psi^-1_br[i] = psi^-br(i) (times 1/2, see Sec. III-A halving) with their
+ * Shoup companions floor(w 2^64 / q), and mu = floor(2^(2m+1)/q) of
+ * Algorithm 4.  Device memory: 32 N + 64 bytes per limb.  Synchronous.
+ * Errors: PM_ERR_N, PM_ERR_Q, PM_ERR_PSI, PM_ERR_OOM, PM_ERR_CUDA. */
+pm_status pm_plan_create(pm_plan **out, uint32_t log2n, uint32_t nlimbs,
+                         const uint64_t *q, const uint64_t *psi, int device);
+
+/* Release the plan and its device memory.  NULL is accepted. */
+pm_status pm_plan_destroy(pm_plan *plan);
+
+/* Pre-size the stream's scratch area for batches of up to npoly
+ * polynomials (N >= 2^14 only; a no-op otherwise).  Synchronous. */
+pm_status pm_plan_reserve(pm_plan *plan, uint32_t npoly, void *stream);
+
+/* Plan facts: N, L, and the plan's moduli/psi (host[nlimbs] each, either
+ * may be NULL). */
+pm_status pm_plan_info(const pm_plan *plan, uint32_t *log2n, uint32_t *nlimbs,
+                       uint64_t *q_out, uint64_t *psi_out);
+
+/* Forward merged CT NTT (Algorithm 6), in place, for every unit of a batch:
+ *   d_x[u*N + j] <- sum_i x_i psi_l^{i (2 br(j) + 1)} mod q_l
+ * i.e. normal order in, bit-reversed order out (no->bo).  npoly >= 1. */
+pm_status pm_ntt_fwd(const pm_plan *plan, uint64_t *d_x, uint32_t npoly, void *stream);
+
+/* Inverse merged GS NTT (Algorithm 7 with the psi^-1 table and the 1/2
+ * scaling at every butterfly, Sec. III-A), in place: the exact inverse of
+ * pm_ntt_fwd (bit-reversed order in, normal order out, 1/N applied). */
+pm_status pm_ntt_inv(const pm_plan *plan, uint64_t *d_x, uint32_t npoly, void *stream);
+
+/* Pointwise (Hadamard) product d_c = d_a . d_b mod q_l, reduced with
+ * Algorithm 4 (at most one correction).  d_c may alias d_a or d_b. */
+pm_status pm_pointwise(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
+                       uint64_t *d_c, uint32_t npoly, void *stream);
+
+/* Negacyclic product of every unit, fused in one launch (Eq. 2): forward
+ * NTT of a and b, pointwise product, inverse NTT with 1/N folded in.
+ * d_a, d_b, d_c: device [npoly][nlimbs][N].  d_c may alias d_a or d_b
+ * (each unit reads all of its inputs before it writes any output). */
+pm_status pm_polymul(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
+                     uint64_t *d_c, uint32_t npoly, void *stream);
+
+/* Same product from and to HOST memory: copies h_a, h_b to the device
+ * buffers d_a, d_b, runs pm_polymul into d_c and copies d_c back to h_c, all
+ * on `stream`, in chunks so that copies and compute of successive chunks
+ * overlap (the plan's internal side streams and events order them).  Host
+ * buffers should be pinned (cudaHostAlloc) for full copy speed.  The call
+ * returns once h_c holds the result (it synchronises `stream`). */
+pm_status pm_polymul_host(const pm_plan *plan, const uint64_t *h_a, const uint64_t *h_b,
+                          uint64_t *h_c, uint64_t *d_a, uint64_t *d_b, uint64_t *d_c,
+                          uint32_t npoly, void *stream);
+
+/* Checks 0 <= x < q_l for every coefficient of d_x [npoly][nlimbs][N];
+ * returns PM_ERR_RANGE if one is out of range.  Synchronous. */
+pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t npoly,
+                           void *stream);
+
+/* Profiling hook for pm_polymul: with n > 0, each later pm_polymul on this
+ * plan records events[k] (cudaEvent_t, created by the caller) on its stream
+ * after phase k: k = 0 before the first kernel, then after each kernel
+ * (column forward, rows, column inverse for N >= 2^14; the single fused
+ * kernel otherwise).  n = 0 turns it off.  n <= 4. */
+pm_status pm_plan_set_phase_events(pm_plan *plan, void *const *events, int n);
+
+/* Wait for all work the plan's calls queued on `stream` and report any
+ * device-side error. */
+pm_status pm_plan_sync(const pm_plan *plan, void *stream);
+
+/* Message for the last failing call on this host thread ("" if none). */
+const char *pm_last_error(void);
+
+/* Copy of pm_last_error() into buf[n] (always NUL-terminated when n > 0). */
+pm_status pm_last_error_string(char *buf, size_t n);
+
+/* Roofline denominators for this integer path, measured on `device`:
+ *   mulmod_per_s : register-resident rate of the lazy Shoup 64-bit modular
+ *                  product (60-bit q) used by the NTT butterflies
+ *   imad_per_s   : 32-bit integer multiply-add rate
+ * Runs two short kernels (tens of milliseconds) and synchronises the device.
+ * The paper measures reductions the same way (Sec. II-B, register-resident
+ * microbenchmarks of one reduction per operation). */
+pm_status pm_measure_peaks(int device, double *mulmod_per_s, double *imad_per_s);
+
+/* Library version string. */
+const char *pm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

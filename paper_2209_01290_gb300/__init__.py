@@ -1,0 +1,145 @@
+"""Exact negacyclic polynomial multiplication on GB300 (sm_103a).
+
+c = a * b in Z_q[X]/(X^N + 1) computed as in arxiv 2209.01290, Eq. 2: merged
+Cooley-Tukey forward NTT (Algorithm 6), pointwise product with the Barrett
+variant of Algorithm 4, merged Gentleman-Sande inverse NTT (Algorithm 7) with
+the 1/N scaling folded in as halvings.  All arithmetic runs in the CUDA
+library built from ``csrc/`` (C ABI in ``include/pm.h``); this package only
+marshals torch tensors (device memory, streams) into that ABI.
+
+Tensors are int64 (or uint64) with values in [0, q_l), shaped
+[npoly, nlimbs, N] (or anything with that many contiguous elements).
+"""
+from __future__ import annotations
+
+from . import capi
+from .capi import PMError, pm_find_params  # noqa: F401
+
+__all__ = ["Plan", "find_params", "PMError", "capi"]
+
+
+def find_params(n: int, nlimbs: int = 1, qbits: int = 60):
+    """(q list, psi list): the nlimbs largest primes q < 2^qbits, q = 1 mod 2N."""
+    return pm_find_params(_log2(n), nlimbs, qbits)
+
+
+def _log2(n: int) -> int:
+    if n < 2 or n & (n - 1):
+        raise ValueError(f"N={n} must be a power of two >= 2")
+    return n.bit_length() - 1
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """A device-resident plan for one (N, {q_l}, {psi_l})."""
+
+    def __init__(self, n: int, qs, psis=None, device: int = 0):
+        self.n = n
+        self.log2n = _log2(n)
+        self.device = device
+        self._h = capi.pm_plan_create(self.log2n, list(qs), psis, device)
+        _, self.nlimbs, self.qs, self.psis = capi.pm_plan_info(self._h)
+
+    # -- lifetime
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            capi.pm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    # -- argument checks (the C side re-checks pointers and sizes)
+    def _npoly(self, t) -> int:
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if t.dtype not in (torch.int64, torch.uint64):
+            raise TypeError(f"expected int64/uint64, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if t.device.index != self.device:
+            raise ValueError(f"tensor on cuda:{t.device.index}, plan on cuda:{self.device}")
+        per = self.nlimbs * self.n
+        if t.numel() == 0 or t.numel() % per:
+            raise ValueError(f"numel {t.numel()} is not a positive multiple of nlimbs*N = {per}")
+        return t.numel() // per
+
+    # -- hot path
+    def ntt_fwd_(self, x, stream=None):
+        npoly = self._npoly(x)
+        capi.pm_ntt_fwd(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+        return x
+
+    def ntt_inv_(self, x, stream=None):
+        npoly = self._npoly(x)
+        capi.pm_ntt_inv(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+        return x
+
+    def pointwise(self, a, b, out=None, stream=None):
+        import torch
+        npoly = self._npoly(a)
+        if self._npoly(b) != npoly:
+            raise ValueError("a and b differ in size")
+        out = torch.empty_like(a) if out is None else out
+        if self._npoly(out) != npoly:
+            raise ValueError("out has the wrong size")
+        capi.pm_pointwise(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly,
+                          _stream_handle(stream))
+        return out
+
+    def polymul(self, a, b, out=None, stream=None):
+        import torch
+        npoly = self._npoly(a)
+        if self._npoly(b) != npoly:
+            raise ValueError("a and b differ in size")
+        out = torch.empty_like(a) if out is None else out
+        if self._npoly(out) != npoly:
+            raise ValueError("out has the wrong size")
+        capi.pm_polymul(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly,
+                        _stream_handle(stream))
+        return out
+
+    def polymul_host(self, h_a, h_b, h_c, d_a, d_b, d_c, stream=None):
+        """Host-to-host product through device buffers (copies pipelined)."""
+        npoly = self._npoly(d_a)
+        for h in (h_a, h_b, h_c):
+            if h.is_cuda or not h.is_contiguous() or h.numel() != d_a.numel():
+                raise ValueError("host tensors must be contiguous CPU tensors of the same size")
+        capi.pm_polymul_host(self.handle, h_a.data_ptr(), h_b.data_ptr(), h_c.data_ptr(),
+                             d_a.data_ptr(), d_b.data_ptr(), d_c.data_ptr(), npoly,
+                             _stream_handle(stream))
+        return h_c
+
+    def reserve(self, npoly: int, stream=None) -> None:
+        capi.pm_plan_reserve(self.handle, npoly, _stream_handle(stream))
+
+    def check_reduced(self, x, stream=None) -> bool:
+        npoly = self._npoly(x)
+        return capi.pm_check_reduced(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+
+    def sync(self, stream=None) -> None:
+        capi.pm_plan_sync(self.handle, _stream_handle(stream))

@@ -1,0 +1,179 @@
+"""ctypes binding of the C ABI in include/pm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and passes
+plain integers/pointers through; all arithmetic runs in libpm_gb300.so.
+Loading fails loudly if the library has not been built or cannot be loaded:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PM_OK = 0
+STATUS_NAMES = {
+    0: "PM_OK", -1: "PM_ERR_ARG", -2: "PM_ERR_N", -3: "PM_ERR_Q", -4: "PM_ERR_PSI",
+    -5: "PM_ERR_CUDA", -6: "PM_ERR_OOM", -7: "PM_ERR_TIMEOUT", -8: "PM_ERR_BUDGET",
+    -9: "PM_ERR_UNSUPPORTED", -10: "PM_ERR_RANGE",
+}
+
+# exported symbol -> (restype, argtypes)
+_u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_vp, _sz = ctypes.c_void_p, ctypes.c_size_t
+_pu64, _pu32 = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)
+SIGNATURES = {
+    "pm_find_params": (_i32, [_u32, _u32, _u32, _pu64, _pu64]),
+    "pm_plan_create": (_i32, [ctypes.POINTER(_vp), _u32, _u32, _pu64, _pu64, _i32]),
+    "pm_plan_destroy": (_i32, [_vp]),
+    "pm_plan_reserve": (_i32, [_vp, _u32, _vp]),
+    "pm_plan_info": (_i32, [_vp, _pu32, _pu32, _pu64, _pu64]),
+    "pm_ntt_fwd": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_ntt_inv": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_pointwise": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_polymul": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_polymul_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_check_reduced": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_plan_sync": (_i32, [_vp, _vp]),
+    "pm_plan_set_phase_events": (_i32, [_vp, ctypes.POINTER(_vp), _i32]),
+    "pm_last_error": (ctypes.c_char_p, []),
+    "pm_last_error_string": (_i32, [ctypes.c_char_p, _sz]),
+    "pm_version": (ctypes.c_char_p, []),
+    "pm_measure_peaks": (_i32, [_i32, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class PMError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libpm_gb300.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libpm_gb300.so not built ({_build.LIB}); run "
+                              "python -m paper_2209_01290_gb300.build")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def check(status: int, where: str) -> None:
+    if status != PM_OK:
+        msg = load().pm_last_error().decode(errors="replace")
+        raise PMError(status, where, msg)
+
+
+def _call(name, *args):
+    st = getattr(load(), name)(*args)
+    check(st, name)
+
+
+def pm_find_params(log2n: int, nlimbs: int, qbits: int = 60):
+    q = (ctypes.c_uint64 * nlimbs)()
+    psi = (ctypes.c_uint64 * nlimbs)()
+    _call("pm_find_params", log2n, nlimbs, qbits, q, psi)
+    return list(q), list(psi)
+
+
+def pm_plan_create(log2n: int, qs, psis=None, device: int = 0) -> int:
+    L = len(qs)
+    q = (ctypes.c_uint64 * L)(*[int(x) for x in qs])
+    p = (ctypes.c_uint64 * L)(*[int(x) for x in psis]) if psis is not None else None
+    out = ctypes.c_void_p()
+    _call("pm_plan_create", ctypes.byref(out), log2n, L, q, p, device)
+    return out.value
+
+
+def pm_plan_destroy(plan: int) -> None:
+    _call("pm_plan_destroy", plan)
+
+
+def pm_plan_reserve(plan: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_plan_reserve", plan, npoly, stream)
+
+
+def pm_plan_info(plan: int):
+    log2n, nl = ctypes.c_uint32(), ctypes.c_uint32()
+    _call("pm_plan_info", plan, ctypes.byref(log2n), ctypes.byref(nl), None, None)
+    L = nl.value
+    q = (ctypes.c_uint64 * L)()
+    psi = (ctypes.c_uint64 * L)()
+    _call("pm_plan_info", plan, None, None, q, psi)
+    return log2n.value, L, list(q), list(psi)
+
+
+def pm_ntt_fwd(plan: int, d_x: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_ntt_fwd", plan, d_x, npoly, stream)
+
+
+def pm_ntt_inv(plan: int, d_x: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_ntt_inv", plan, d_x, npoly, stream)
+
+
+def pm_pointwise(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_pointwise", plan, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_polymul(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_polymul", plan, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_polymul_host(plan: int, h_a: int, h_b: int, h_c: int, d_a: int, d_b: int, d_c: int,
+                    npoly: int, stream: int = 0) -> None:
+    _call("pm_polymul_host", plan, h_a, h_b, h_c, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_check_reduced(plan: int, d_x: int, npoly: int, stream: int = 0) -> bool:
+    st = load().pm_check_reduced(plan, d_x, npoly, stream)
+    if st == -10:
+        return False
+    check(st, "pm_check_reduced")
+    return True
+
+
+def pm_plan_set_phase_events(plan: int, events) -> None:
+    """events: list of cudaEvent_t handles (ints), at most 4; [] turns it off."""
+    arr = (ctypes.c_void_p * max(1, len(events)))(*[int(e) for e in events])
+    _call("pm_plan_set_phase_events", plan, arr, len(events))
+
+
+def pm_plan_sync(plan: int, stream: int = 0) -> None:
+    _call("pm_plan_sync", plan, stream)
+
+
+def pm_last_error() -> str:
+    return load().pm_last_error().decode(errors="replace")
+
+
+def pm_measure_peaks(device: int = 0):
+    """(Shoup mulmods/s, 32-bit IMAD/s) measured on `device`."""
+    m, i = ctypes.c_double(), ctypes.c_double()
+    st = load().pm_measure_peaks(device, ctypes.byref(m), ctypes.byref(i))
+    check(st, "pm_measure_peaks")
+    return m.value, i.value
+
+
+def pm_version() -> str:
+    return load().pm_version().decode()

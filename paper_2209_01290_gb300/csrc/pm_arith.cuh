@@ -1,0 +1,89 @@
+// pm_arith.cuh -- device modular arithmetic for 64-bit words and moduli
+// q < 2^62 (arxiv 2209.01290, Sec. II).
+//
+// Value ranges ("lazy" representatives, Harvey-style) used by the butterflies:
+//   forward CT butterfly : inputs and outputs in [0, 4q)
+//   inverse GS butterfly : inputs and outputs in [0, 2q)
+// q < 2^62 keeps 4q < 2^64, so no word ever overflows.  Results that leave
+// the library are reduced to the canonical range [0, q).
+#pragma once
+#include <cstdint>
+
+#include "pm_types.h"
+
+namespace pm {
+
+__device__ __forceinline__ TwPair ld_tw(const TwPair* __restrict__ p) {
+  ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
+  return TwPair{v.x, v.y};
+}
+
+// w * y mod q up to one multiple of q (Shoup): for w < q and any 64-bit y,
+// the result is congruent to w*y and lies in [0, 2q).
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint64_t wp,
+                                                   uint64_t q) {
+  const uint64_t qh = __umul64hi(wp, y);
+  return w * y - qh * q;
+}
+
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
+
+// Merged-CT butterfly (Algorithm 6 body):
+//   (x, y) <- (x + w y, x - w y) mod q
+// on lazy representatives in [0, 4q).
+__device__ __forceinline__ void ct_bfly(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
+                                        uint64_t q, uint64_t two_q) {
+  const uint64_t a = csub(x, two_q);               // [0, 2q)
+  const uint64_t t = mul_shoup_lazy(y, w, wp, q);  // [0, 2q)
+  x = a + t;                                       // [0, 4q)
+  y = a - t + two_q;                               // (0, 4q)
+}
+
+// x/2 mod q for x in [0, 2q): x >> 1 plus (q+1)/2 when x is odd (Sec. III-A).
+// Result in [0, 2q).
+__device__ __forceinline__ uint64_t half_lazy(uint64_t x, uint64_t half_q1) {
+  return (x >> 1) + ((x & 1) ? half_q1 : 0);
+}
+
+// Merged-GS butterfly (Algorithm 7 body) with the 1/2 scaling of Eq. 2:
+//   (x, y) <- ((x + y)/2, w (x - y)/2) mod q
+// w2 = w * 2^-1 mod q is the table entry, so the second output needs no
+// separate halving.  Lazy representatives in [0, 2q).
+__device__ __forceinline__ void gs_bfly_half(uint64_t& x, uint64_t& y, uint64_t w2,
+                                             uint64_t w2p, uint64_t q, uint64_t two_q,
+                                             uint64_t half_q1) {
+  const uint64_t s = csub(x + y, two_q);           // [0, 2q)
+  const uint64_t d = x - y + two_q;                // (0, 4q)
+  x = half_lazy(s, half_q1);                       // [0, 2q)
+  y = mul_shoup_lazy(d, w2, w2p, q);               // [0, 2q)
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q, uint64_t two_q) {
+  return csub(csub(x, two_q), q);
+}
+
+// Algorithm 4 (the paper's Barrett variant): x = a*b < 2^(2m) for a, b < q,
+//   c = x >> (m-2); quot = (c * mu) >> (m+3); rem = x - quot*q; one correction.
+// The 128-bit quantities are kept as (hi, lo) pairs; only the low word of
+// quot*q is needed because rem < 2q < 2^64.
+__device__ __forceinline__ uint64_t mul_barrett_alg4(uint64_t a, uint64_t b,
+                                                     const LimbConst& k) {
+  const uint64_t lo = a * b;
+  const uint64_t hi = __umul64hi(a, b);
+  // c = x >> (m-2); 1 <= m-2 <= 60
+  const uint64_t c = (lo >> k.sh1) | (hi << (64 - k.sh1));
+  const uint64_t plo = c * k.mu;
+  const uint64_t phi = __umul64hi(c, k.mu);
+  // quot = (phi:plo) >> (m+3); m+3 ranges over [6, 65]
+  uint64_t quot;
+  if (k.sh2 >= 64) {
+    quot = phi >> (k.sh2 - 64);
+  } else {
+    quot = (plo >> k.sh2) | (phi << (64 - k.sh2));
+  }
+  const uint64_t rem = lo - quot * k.q;
+  return csub(rem, k.q);
+}
+
+}  // namespace pm

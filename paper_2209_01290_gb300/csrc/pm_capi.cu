@@ -1,0 +1,508 @@
+// pm_capi.cu -- the C ABI declared in include/pm.h: plan lifetime, argument
+// validation, error reporting and dispatch to the kernels.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "pm_internal.h"
+#include "pm_params.h"
+
+#define PM_VERSION "0.1.0"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pm_status fail(pm_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+pm_status ok() {
+  g_err[0] = '\0';
+  return PM_OK;
+}
+
+pm_status cuda_fail(cudaError_t e, const char* what) {
+  const pm_status st = (e == cudaErrorMemoryAllocation) ? PM_ERR_OOM : PM_ERR_CUDA;
+  return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Makes `dev` current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+std::mutex g_prep_mu;
+std::vector<int> g_prepared;  // devices on which kernels_prepare() ran
+
+cudaError_t prepare_device(int dev) {
+  std::lock_guard<std::mutex> lk(g_prep_mu);
+  for (int d : g_prepared)
+    if (d == dev) return cudaSuccess;
+  cudaError_t e = pm::kernels_prepare();
+  if (e == cudaSuccess) g_prepared.push_back(dev);
+  return e;
+}
+
+constexpr uint32_t kMaxLog2N = 17;
+constexpr uint32_t kMaxLimbs = 1024;
+constexpr int kHostChunks = 8;
+
+}  // namespace
+
+struct pm_plan {
+  int device = 0;
+  int num_sms = 0;
+  uint32_t logn = 0, nlimbs = 0;
+  std::vector<uint64_t> q, psi;
+  pm::LimbConst* d_lc = nullptr;
+  pm::TwPair* d_twf = nullptr;
+  pm::TwPair* d_twi = nullptr;
+  int* d_flag = nullptr;
+  std::mutex mu;  // guards the scratch list and the host-pipeline objects
+  // Scratch for the column-split polymul path, one area per stream so that
+  // calls on different streams never share it (calls on one stream are
+  // ordered by the stream).
+  struct Scratch {
+    cudaStream_t stream;
+    uint64_t* ptr;
+    uint64_t units;
+  };
+  std::vector<Scratch> scratch;
+  cudaStream_t side_in = nullptr, side_out = nullptr;
+  cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {}, ev_start = nullptr,
+              ev_end = nullptr;
+  pm::PhaseEvents phase{};  // profiling hook (pm_plan_set_phase_events)
+};
+
+namespace {
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+pm_status check_plan(const pm_plan* p) {
+  if (!p) return fail(PM_ERR_ARG, "plan is NULL");
+  return PM_OK;
+}
+
+pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
+  pm::KParams P{};
+  P.twf = p->d_twf;
+  P.twi = p->d_twi;
+  P.lc = p->d_lc;
+  P.logn = p->logn;
+  P.nlimbs = p->nlimbs;
+  P.nunits = npoly * p->nlimbs;
+  return P;
+}
+
+pm_status check_batch(const pm_plan* p, uint32_t npoly) {
+  if (npoly == 0) return fail(PM_ERR_ARG, "npoly must be >= 1");
+  const uint64_t units = (uint64_t)npoly * p->nlimbs;
+  if (units > 0x7fffffffull >> (p->logn > 12 ? p->logn - 12 : 0))
+    return fail(PM_ERR_ARG, "batch too large: %llu units", (unsigned long long)units);
+  return PM_OK;
+}
+
+// The stream's scratch area, grown to at least `units` polynomials (caller
+// holds p->mu).  Growing frees the old area (cudaFree synchronises the
+// device) and allocates a new one.
+pm_status ensure_scratch(pm_plan* p, cudaStream_t st, uint64_t units, uint64_t** out) {
+  pm_plan::Scratch* sc = nullptr;
+  for (auto& s : p->scratch)
+    if (s.stream == st) sc = &s;
+  if (!sc) {
+    p->scratch.push_back(pm_plan::Scratch{st, nullptr, 0});
+    sc = &p->scratch.back();
+  }
+  if (units > sc->units) {
+    if (sc->ptr) {
+      cudaError_t e = cudaFree(sc->ptr);
+      sc->ptr = nullptr;
+      sc->units = 0;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFree(scratch)");
+    }
+    cudaError_t e = cudaMalloc(&sc->ptr, (size_t)units << p->logn << 3);
+    if (e != cudaSuccess) {
+      sc->ptr = nullptr;
+      return cuda_fail(e, "cudaMalloc(scratch)");
+    }
+    sc->units = units;
+  }
+  *out = sc->ptr;
+  return PM_OK;
+}
+
+void destroy_plan(pm_plan* p) {
+  if (!p) return;
+  DeviceGuard g(p->device);
+  cudaFree(p->d_lc);
+  cudaFree(p->d_twf);
+  cudaFree(p->d_twi);
+  cudaFree(p->d_flag);
+  for (auto& sc : p->scratch) cudaFree(sc.ptr);
+  if (p->side_in) cudaStreamDestroy(p->side_in);
+  if (p->side_out) cudaStreamDestroy(p->side_out);
+  for (int i = 0; i < kHostChunks; ++i) {
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_end) cudaEventDestroy(p->ev_end);
+  delete p;
+}
+
+pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
+                       uint32_t npoly, cudaStream_t st) {
+  pm::KParams P = base_params(p, npoly);
+  P.a = d_a;
+  P.b = d_b;
+  P.c = d_c;
+  if (pm::polymul_needs_scratch(p->logn)) {
+    pm_status s = ensure_scratch(p, st, P.nunits, &P.s);
+    if (s != PM_OK) return s;
+  }
+  cudaError_t e = pm::launch_polymul(P, st, p->phase.n ? &p->phase : nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "polymul launch");
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pm_version(void) { return PM_VERSION; }
+
+const char* pm_last_error(void) { return g_err; }
+
+pm_status pm_last_error_string(char* buf, size_t n) {
+  if (!buf || n == 0) return PM_ERR_ARG;
+  snprintf(buf, n, "%s", g_err);
+  return PM_OK;
+}
+
+pm_status pm_find_params(uint32_t log2n, uint32_t nlimbs, uint32_t qbits, uint64_t* q_out,
+                         uint64_t* psi_out) {
+  if (log2n < 1 || log2n > kMaxLog2N) return fail(PM_ERR_N, "log2n=%u outside [1,17]", log2n);
+  if (nlimbs < 1 || nlimbs > kMaxLimbs) return fail(PM_ERR_ARG, "nlimbs=%u outside [1,1024]", nlimbs);
+  if (qbits < 3 || qbits > 62 || qbits <= log2n + 1)
+    return fail(PM_ERR_Q, "qbits=%u invalid for log2n=%u (need log2n+1 < qbits <= 62)", qbits, log2n);
+  if (!q_out) return fail(PM_ERR_ARG, "q_out is NULL");
+  std::vector<uint64_t> qs(nlimbs);
+  const int got = pm::host::largest_ntt_primes(log2n, qbits, nlimbs, qs.data());
+  if (got < (int)nlimbs)
+    return fail(PM_ERR_Q, "only %d primes q < 2^%u with q = 1 mod 2^%u", got, qbits, log2n + 1);
+  for (uint32_t i = 0; i < nlimbs; ++i) {
+    q_out[i] = qs[i];
+    if (psi_out) {
+      psi_out[i] = pm::host::default_psi(qs[i], log2n);
+      if (!psi_out[i]) return fail(PM_ERR_PSI, "no psi found for q=%llu", (unsigned long long)qs[i]);
+    }
+  }
+  return ok();
+}
+
+pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const uint64_t* q,
+                         const uint64_t* psi, int device) {
+  if (!out) return fail(PM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (log2n < 1 || log2n > kMaxLog2N) return fail(PM_ERR_N, "log2n=%u outside [1,17]", log2n);
+  if (nlimbs < 1 || nlimbs > kMaxLimbs) return fail(PM_ERR_ARG, "nlimbs=%u outside [1,1024]", nlimbs);
+  if (!q) return fail(PM_ERR_ARG, "q is NULL");
+  const uint64_t n = (uint64_t)1 << log2n;
+  std::vector<uint64_t> psis(nlimbs);
+  for (uint32_t l = 0; l < nlimbs; ++l) {
+    const uint64_t ql = q[l];
+    if (ql <= 3 || ql >= ((uint64_t)1 << 62))
+      return fail(PM_ERR_Q, "limb %u: q=%llu outside (3, 2^62)", l, (unsigned long long)ql);
+    if ((ql - 1) % (2 * n))
+      return fail(PM_ERR_Q, "limb %u: q=%llu is not 1 mod 2N (N=%llu)", l, (unsigned long long)ql,
+                  (unsigned long long)n);
+    if (!pm::host::is_prime_u64(ql))
+      return fail(PM_ERR_Q, "limb %u: q=%llu is not prime", l, (unsigned long long)ql);
+    if (psi) {
+      const uint64_t p = psi[l];
+      if (p == 0 || p >= ql || pm::host::pow_mod(p, n, ql) != ql - 1)
+        return fail(PM_ERR_PSI, "limb %u: psi=%llu is not a primitive 2N-th root mod q", l,
+                    (unsigned long long)p);
+      psis[l] = p;
+    } else {
+      psis[l] = pm::host::default_psi(ql, log2n);
+      if (!psis[l]) return fail(PM_ERR_PSI, "limb %u: no psi found", l);
+    }
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(PM_ERR_ARG, "device %d not present (%d devices)", device, ndev);
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = new (std::nothrow) pm_plan();
+  if (!p) return fail(PM_ERR_OOM, "host allocation failed");
+  p->device = device;
+  p->logn = log2n;
+  p->nlimbs = nlimbs;
+  p->q.assign(q, q + nlimbs);
+  p->psi = psis;
+  e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  e = prepare_device(device);
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_fail(e, "kernel attributes");
+  }
+  std::vector<pm::LimbConst> lc(nlimbs);
+  std::vector<pm::TwPair> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
+  for (uint32_t l = 0; l < nlimbs; ++l)
+    pm::host::build_limb(log2n, q[l], psis[l], &lc[l], &twf[(size_t)l * n], &twi[(size_t)l * n]);
+  const size_t tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair);
+  if ((e = cudaMalloc(&p->d_lc, nlimbs * sizeof(pm::LimbConst))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_twf, tw_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_twi, tw_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_flag, sizeof(int))) != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_fail(e, "cudaMalloc(plan tables)");
+  }
+  if ((e = cudaMemcpy(p->d_lc, lc.data(), nlimbs * sizeof(pm::LimbConst), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(p->d_twf, twf.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_twi, twi.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_fail(e, "cudaMemcpy(plan tables)");
+  }
+  *out = p;
+  return ok();
+}
+
+pm_status pm_plan_destroy(pm_plan* plan) {
+  destroy_plan(plan);
+  return ok();
+}
+
+pm_status pm_plan_info(const pm_plan* plan, uint32_t* log2n, uint32_t* nlimbs, uint64_t* q_out,
+                       uint64_t* psi_out) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (log2n) *log2n = plan->logn;
+  if (nlimbs) *nlimbs = plan->nlimbs;
+  for (uint32_t l = 0; l < plan->nlimbs; ++l) {
+    if (q_out) q_out[l] = plan->q[l];
+    if (psi_out) psi_out[l] = plan->psi[l];
+  }
+  return ok();
+}
+
+pm_status pm_plan_reserve(pm_plan* plan, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  if (!pm::polymul_needs_scratch(plan->logn)) return ok();
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  uint64_t* ptr = nullptr;
+  s = ensure_scratch(plan, (cudaStream_t)stream, (uint64_t)npoly * plan->nlimbs, &ptr);
+  return s == PM_OK ? ok() : s;
+}
+
+pm_status pm_ntt_fwd(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = d_x;
+  P.c = d_x;
+  cudaError_t e = pm::launch_ntt_fwd(P, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ntt_fwd launch");
+  return ok();
+}
+
+pm_status pm_ntt_inv(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = d_x;
+  P.c = d_x;
+  cudaError_t e = pm::launch_ntt_inv(P, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ntt_inv launch");
+  return ok();
+}
+
+pm_status pm_pointwise(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
+                       uint64_t* d_c, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = d_a;
+  P.b = d_b;
+  P.c = d_c;
+  cudaError_t e = pm::launch_pointwise(P, (cudaStream_t)stream, plan->num_sms);
+  if (e != cudaSuccess) return cuda_fail(e, "pointwise launch");
+  return ok();
+}
+
+pm_status pm_polymul(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
+                     uint64_t* d_c, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  s = polymul_impl(p, d_a, d_b, d_c, npoly, (cudaStream_t)stream);
+  return s == PM_OK ? ok() : s;
+}
+
+pm_status pm_polymul_host(const pm_plan* plan, const uint64_t* h_a, const uint64_t* h_b,
+                          uint64_t* h_c, uint64_t* d_a, uint64_t* d_b, uint64_t* d_c,
+                          uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!h_a || !h_b || !h_c || !d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) ||
+      !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  cudaError_t e;
+  if (!p->side_in) {
+    if ((e = cudaStreamCreateWithFlags(&p->side_in, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&p->side_out, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->ev_end, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "pipeline streams");
+    for (int i = 0; i < kHostChunks; ++i)
+      if ((e = cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "pipeline events");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  uint64_t* scratch = nullptr;
+  if (pm::polymul_needs_scratch(p->logn)) {
+    s = ensure_scratch(p, st, (uint64_t)npoly * p->nlimbs, &scratch);
+    if (s != PM_OK) return s;
+  }
+  const size_t poly_words = (size_t)p->nlimbs << p->logn;
+  const uint32_t nchunks = npoly < (uint32_t)kHostChunks ? npoly : (uint32_t)kHostChunks;
+  // the side streams start after work already queued on `st`
+  if ((e = cudaEventRecord(p->ev_start, st)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(p->side_in, p->ev_start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(p->side_out, p->ev_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "pipeline start");
+  uint32_t done = 0;
+  for (uint32_t k = 0; k < nchunks; ++k) {
+    const uint32_t cnt = (npoly - done) / (nchunks - k);
+    const size_t off = (size_t)done * poly_words, bytes = (size_t)cnt * poly_words * 8;
+    if ((e = cudaMemcpyAsync(d_a + off, h_a + off, bytes, cudaMemcpyHostToDevice, p->side_in)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(d_b + off, h_b + off, bytes, cudaMemcpyHostToDevice, p->side_in)) !=
+            cudaSuccess ||
+        (e = cudaEventRecord(p->ev_in[k], p->side_in)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, p->ev_in[k], 0)) != cudaSuccess)
+      return cuda_fail(e, "pipeline copy-in");
+    // the scratch is indexed from unit 0 of each launch; chunks run in order on `st`
+    pm::KParams P = base_params(p, cnt);
+    P.a = d_a + off;
+    P.b = d_b + off;
+    P.c = d_c + off;
+    P.s = scratch;
+    if ((e = pm::launch_polymul(P, st)) != cudaSuccess) return cuda_fail(e, "polymul launch");
+    if ((e = cudaEventRecord(p->ev_done[k], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->side_out, p->ev_done[k], 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h_c + off, d_c + off, bytes, cudaMemcpyDeviceToHost, p->side_out)) !=
+            cudaSuccess)
+      return cuda_fail(e, "pipeline copy-out");
+    done += cnt;
+  }
+  if ((e = cudaEventRecord(p->ev_end, p->side_out)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(st, p->ev_end, 0)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "pipeline end");
+  return ok();
+}
+
+pm_status pm_check_reduced(const pm_plan* plan, const uint64_t* d_x, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_x) return fail(PM_ERR_ARG, "d_x is NULL");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  pm::KParams P = base_params(p, npoly);
+  P.a = d_x;
+  int flag = 0;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = pm::launch_check_reduced(P, p->d_flag, st, p->num_sms)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "check_reduced");
+  if (flag) return fail(PM_ERR_RANGE, "a coefficient is >= its modulus");
+  return ok();
+}
+
+pm_status pm_plan_set_phase_events(pm_plan* plan, void* const* events, int n) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (n < 0 || n > 4 || (n > 0 && !events)) return fail(PM_ERR_ARG, "n must be 0..4");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  plan->phase.n = n;
+  for (int k = 0; k < n; ++k) plan->phase.ev[k] = (cudaEvent_t)events[k];
+  return ok();
+}
+
+pm_status pm_plan_sync(const pm_plan* plan, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "device error");
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// pm_internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "pm_arith.cuh"
+
+namespace pm {
+
+enum Mode { MODE_POLYMUL = 0, MODE_FWD = 1, MODE_INV = 2 };
+
+// Kernel parameters for one batched call on one plan.
+struct KParams {
+  const uint64_t* a;     // operand a (device), [nunits][N]
+  const uint64_t* b;     // operand b
+  uint64_t* c;           // output / in-place buffer
+  uint64_t* s;           // scratch [nunits][N] for the column-split path
+  const TwPair* twf;     // [nlimbs][N] forward twiddles Psi_br with Shoup companions
+  const TwPair* twi;     // [nlimbs][N] inverse twiddles Psi^-1_br * 1/2 with companions
+  const LimbConst* lc;   // [nlimbs]
+  uint32_t logn;
+  uint32_t nlimbs;
+  uint32_t nunits;       // npoly * nlimbs
+  uint32_t pad;
+};
+
+// Optional profiling hook: when set, the launcher records ev[k] on the
+// launch stream after phase k of a polymul (k < n).  Host-side only.
+struct PhaseEvents {
+  cudaEvent_t ev[4];
+  int n;
+};
+
+cudaError_t kernels_prepare();
+cudaError_t launch_polymul(const KParams& P, cudaStream_t st,
+                           const PhaseEvents* pe = nullptr);
+cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st);
+cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st);
+cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms);
+cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st, int num_sms);
+
+// True when the polymul path for this N needs the [nunits][N] scratch.
+inline bool polymul_needs_scratch(uint32_t logn) { return logn >= 14; }
+
+}  // namespace pm

@@ -1,0 +1,701 @@
+// pm_kernels.cu -- sm_103a kernels for exact negacyclic polynomial
+// multiplication (arxiv 2209.01290, Eq. 2):
+//   c = NTT^{GS,psi^-1}_{bo->no,1/2}( NTT^{CT,psi}_{no->bo}(a) . NTT^{CT,psi}_{no->bo}(b) ).
+//
+// Decomposition of one N = 2^n point merged transform (n >= 12)
+// ----------------------------------------------------------------
+// View the N words as R = N/4096 rows of 4096.  In Algorithm 6 (forward, k
+// halving from N/2) the first n-12 stages have strides k >= 4096: they mix
+// only the R words of one column {c + 4096 t}, and all columns use the same
+// twiddles Psi_br[1 .. R-1].  The remaining 12 stages have k < 4096 and act
+// inside one row t; their twiddle for row t, stage s and block i' is
+// Psi_br[2^s + t 2^(s-n+12) + i'] (Algorithm 6's Psi_br[m + i] with the
+// block index i split into row and in-row parts).  Algorithm 7 (inverse, k
+// doubling from 1) is the mirror image: 12 in-row stages first, then n-12
+// column stages.  No extra twiddle multiplication appears at the split
+// (unlike a classical four-step FFT), because the merged transforms keep the
+// psi-powers inside the butterflies.
+//
+// Kernels
+//   k_col_fwd<R>    : the n-12 forward column stages, streaming (registers
+//                     only, coalesced loads/stores), one thread per column.
+//   k_rows<MODE>    : the 12 in-row stages as three radix-16 passes; each
+//                     thread keeps 16 words per operand in registers and
+//                     rows are exchanged through padded shared memory between
+//                     passes.  For polymul the last forward pass, the
+//                     Barrett product (Algorithm 4) and the first inverse pass
+//                     run back to back in registers.
+//   k_col_inv<R>    : the n-12 inverse column stages and the final reduction.
+//   k_fused13       : N = 2^13 in one CTA (column stage through smem).
+//   k_small         : N <= 2^11, one CTA per unit, radix-2 stages in smem.
+//   k_pointwise     : stand-alone Hadamard product with Algorithm 4.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "pm_arith.cuh"
+#include "pm_internal.h"
+
+namespace pm {
+
+constexpr int kRowLog = 12;
+constexpr int kRow = 1 << kRowLog;        // 4096 words per row
+constexpr int kRowPad = kRow + kRow / 32;  // one pad word per 32: conflict-free passes
+
+__device__ __forceinline__ int padj(int j) { return j + (j >> 5); }
+
+// ------------------------------------------------------------------ passes
+
+// Four consecutive merged-CT stages (Algorithm 6) on a register group of 16
+// words.  Global stages s0..s0+3; the group lies in the (N >> s0)-word block
+// number g, its 16 words spaced N >> (s0+4) apart.  Stage s0+st pairs
+// (u, u + 8 >> st) with twiddle Psi_br[2^(s0+st) + g 2^st + (u >> (4-st))].
+// (Stages are template parameters so every register index is a constant.)
+template <int ST, int NOPS>
+__device__ __forceinline__ void ct16_stage(uint64_t (&v)[2][16], const TwPair* __restrict__ tw,
+                                           uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
+  constexpr int h = 8 >> ST;
+  const uint32_t base = (1u << (s0 + ST)) + (g << ST);
+#pragma unroll
+  for (int blk = 0; blk < (1 << ST); blk++) {
+    const TwPair t = ld_tw(tw + base + blk);
+#pragma unroll
+    for (int u0 = 0; u0 < h; u0++) {
+#pragma unroll
+      for (int o = 0; o < NOPS; o++)
+        ct_bfly(v[o][blk * 2 * h + u0], v[o][blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+    }
+  }
+}
+
+template <int NOPS>
+__device__ __forceinline__ void ct16(uint64_t (&v)[2][16], const TwPair* __restrict__ tw,
+                                     uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
+  ct16_stage<0, NOPS>(v, tw, s0, g, q, two_q);
+  ct16_stage<1, NOPS>(v, tw, s0, g, q, two_q);
+  ct16_stage<2, NOPS>(v, tw, s0, g, q, two_q);
+  ct16_stage<3, NOPS>(v, tw, s0, g, q, two_q);
+}
+
+// Four consecutive merged-GS stages (Algorithm 7, 1/2-scaled) on a group of
+// 16 words.  GS stages sig0..sig0+3 (k = 2^sig); the group is block g of
+// 2^(sig0+4) words.  Stage sig0+st pairs (u, u + 2^st) with twiddle
+// Psi^-1_br[(N >> (sig0+st+1)) + g 2^(3-st) + (u >> (st+1))] (times 1/2).
+template <int ST>
+__device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __restrict__ tw,
+                                           uint32_t logn, uint32_t sig0, uint32_t g,
+                                           uint64_t q, uint64_t two_q, uint64_t hq) {
+  constexpr int h = 1 << ST;
+  const uint32_t base = (1u << (logn - sig0 - ST - 1)) + (g << (3 - ST));
+#pragma unroll
+  for (int blk = 0; blk < (8 >> ST); blk++) {
+    const TwPair t = ld_tw(tw + base + blk);
+#pragma unroll
+    for (int u0 = 0; u0 < h; u0++)
+      gs_bfly_half(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
+  }
+}
+
+__device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
+                                     uint32_t logn, uint32_t sig0, uint32_t g,
+                                     uint64_t q, uint64_t two_q, uint64_t hq) {
+  gs16_stage<0>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<1>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<2>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<3>(v, tw, logn, sig0, g, q, two_q, hq);
+}
+
+// Merged CT on a column of R words (the first log2 R stages of the N-point
+// transform): stage s pairs (t, t + R >> (s+1)) with twiddle Psi_br[2^s + blk].
+template <int R, int S>
+__device__ __forceinline__ void ct_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
+                                             uint64_t q, uint64_t two_q) {
+  if constexpr ((1 << S) < R) {
+    constexpr int h = R >> (S + 1);
+#pragma unroll
+    for (int blk = 0; blk < (1 << S); blk++) {
+      const TwPair t = ld_tw(tw + (1u << S) + blk);
+#pragma unroll
+      for (int u0 = 0; u0 < h; u0++)
+        ct_bfly(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+    }
+    ct_col_stage<R, S + 1>(x, tw, q, two_q);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void ct_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
+                                       uint64_t q, uint64_t two_q) {
+  ct_col_stage<R, 0>(x, tw, q, two_q);
+}
+
+// Merged GS on a column of R words (the last log2 R stages): the GS stage
+// with k = 4096 * 2^E pairs (t, t + 2^E) with twiddle
+// Psi^-1_br[(R >> (E+1)) + (t >> (E+1))] (times 1/2).
+template <int R, int E>
+__device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
+                                             uint64_t q, uint64_t two_q, uint64_t hq) {
+  if constexpr ((1 << E) < R) {
+    constexpr int h = 1 << E;
+#pragma unroll
+    for (int blk = 0; blk < R / (2 * h); blk++) {
+      const TwPair t = ld_tw(tw + (R >> (E + 1)) + blk);
+#pragma unroll
+      for (int u0 = 0; u0 < h; u0++)
+        gs_bfly_half(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
+    }
+    gs_col_stage<R, E + 1>(x, tw, q, two_q, hq);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void gs_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
+                                       uint64_t q, uint64_t two_q, uint64_t hq) {
+  gs_col_stage<R, 0>(x, tw, q, two_q, hq);
+}
+
+__device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
+  LimbConst k;
+  const ulonglong2* s = reinterpret_cast<const ulonglong2*>(p);
+  ulonglong2 v0 = __ldg(s), v1 = __ldg(s + 1), v2 = __ldg(s + 2);
+  k.q = v0.x;
+  k.two_q = v0.y;
+  k.half_q1 = v1.x;
+  k.mu = v1.y;
+  k.m = (uint32_t)v2.x;
+  k.sh1 = (uint32_t)(v2.x >> 32);
+  k.sh2 = (uint32_t)v2.y;
+  k.pad0 = 0;
+  return k;
+}
+
+// ----------------------------------------------------------- row pipeline
+
+// Register/smem pipeline for the 12 in-row stages of one 4096-word row (row
+// t of a unit of 2^logn words).  256 threads per row; thread th owns
+//   pass A (P0 / Q2): words th + 256 u            (u = 0..15)
+//   pass B (P1 / Q1): words 256 (th>>4) + (th&15) + 16 u
+//   pass C (P2 / Q0): words 16 th + u
+// which are all bank-conflict free with the 1-in-32 padding.
+struct RowIO {
+  const uint64_t* ga;  // global row of operand a (pass A source), or null
+  const uint64_t* gb;  // global row of operand b
+  uint64_t* gc;        // global row of the output
+  uint64_t* sa;        // smem row buffer, operand a / result
+  uint64_t* sb;        // smem row buffer, operand b
+};
+
+// MODE_FWD: rows of x -> P0..P2 -> canonical bo-order row (global, pass C
+// layout).  MODE_INV: x rows -> Q0..Q2 -> output.  MODE_POLYMUL: a, b rows ->
+// P0..P2 -> Barrett -> Q0..Q2 -> output.
+// SRC_SMEM: P0 (or Q0 for INV) reads the smem buffers instead of global.
+// DST_SMEM: Q2 writes the smem buffer instead of global (lazy [0,2q) kept);
+// otherwise Q2 writes global, canonical if FINAL else lazy.
+template <int MODE, bool SRC_SMEM, bool DST_SMEM, bool FINAL>
+__device__ __forceinline__ void row_pipeline(const RowIO& io, const TwPair* __restrict__ twf,
+                                             const TwPair* __restrict__ twi,
+                                             const LimbConst& K, uint32_t logn, uint32_t t,
+                                             int th) {
+  const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
+  uint64_t v[2][16];
+  const int g1 = th >> 4, o1 = th & 15;
+  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
+    constexpr int NOPS = (MODE == MODE_POLYMUL) ? 2 : 1;
+    // ---- P0: CT stages n-12 .. n-9, pass A layout
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int j = th + 256 * u;
+      if (SRC_SMEM) {
+        v[0][u] = io.sa[padj(j)];
+        if (NOPS == 2) v[1][u] = io.sb[padj(j)];
+      } else {
+        v[0][u] = __ldcs(io.ga + j);
+        if (NOPS == 2) v[1][u] = __ldcs(io.gb + j);
+      }
+    }
+    ct16<NOPS>(v, twf, logn - 12, t, q, two_q);
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int j = padj(th + 256 * u);
+      io.sa[j] = v[0][u];
+      if (NOPS == 2) io.sb[j] = v[1][u];
+    }
+    __syncthreads();
+    // ---- P1: CT stages n-8 .. n-5, pass B layout
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int j = padj(256 * g1 + o1 + 16 * u);
+      v[0][u] = io.sa[j];
+      if (NOPS == 2) v[1][u] = io.sb[j];
+    }
+    ct16<NOPS>(v, twf, logn - 8, t * 16 + g1, q, two_q);
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int j = padj(256 * g1 + o1 + 16 * u);
+      io.sa[j] = v[0][u];
+      if (NOPS == 2) io.sb[j] = v[1][u];
+    }
+    __syncthreads();
+    // ---- P2: CT stages n-4 .. n-1, pass C layout
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const int j = padj(16 * th + u);
+      v[0][u] = io.sa[j];
+      if (NOPS == 2) v[1][u] = io.sb[j];
+    }
+    ct16<NOPS>(v, twf, logn - 4, t * 256 + th, q, two_q);
+    if constexpr (MODE == MODE_FWD) {
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(io.gc + 16 * th);
+#pragma unroll
+      for (int u = 0; u < 16; u += 2)
+        __stcs(dst + u / 2, make_ulonglong2(reduce4(v[0][u], q, two_q),
+                                            reduce4(v[0][u + 1], q, two_q)));
+      return;
+    }
+    // ---- pointwise product (Algorithm 4), bit-reversed order
+#pragma unroll
+    for (int u = 0; u < 16; u++)
+      v[0][u] = mul_barrett_alg4(reduce4(v[0][u], q, two_q), reduce4(v[1][u], q, two_q), K);
+  } else {
+    // MODE_INV: Q0 input in pass C layout
+    if (SRC_SMEM) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(16 * th + u)];
+    } else {
+      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(io.ga + 16 * th);
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        const ulonglong2 w = __ldcs(src + u / 2);
+        v[0][u] = w.x;
+        v[0][u + 1] = w.y;
+      }
+    }
+  }
+  // ---- Q0: GS stages 0..3 (k = 1..8), pass C layout
+  gs16(v[0], twi, logn, 0, t * 256 + th, q, two_q, hq);
+#pragma unroll
+  for (int u = 0; u < 16; u++) io.sa[padj(16 * th + u)] = v[0][u];
+  __syncthreads();
+  // ---- Q1: GS stages 4..7, pass B layout
+#pragma unroll
+  for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(256 * g1 + o1 + 16 * u)];
+  gs16(v[0], twi, logn, 4, t * 16 + g1, q, two_q, hq);
+#pragma unroll
+  for (int u = 0; u < 16; u++) io.sa[padj(256 * g1 + o1 + 16 * u)] = v[0][u];
+  __syncthreads();
+  // ---- Q2: GS stages 8..11, pass A layout
+#pragma unroll
+  for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(th + 256 * u)];
+  gs16(v[0], twi, logn, 8, t, q, two_q, hq);
+  if constexpr (DST_SMEM) {
+#pragma unroll
+    for (int u = 0; u < 16; u++) io.sa[padj(th + 256 * u)] = v[0][u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; u++)
+      __stcs(io.gc + th + 256 * u, FINAL ? csub(v[0][u], q) : v[0][u]);
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+// In-row stages for n >= 12.  One CTA = one row (256 threads).  For n == 12
+// the row is the whole unit (MODE_POLYMUL reads a, b; output canonical).
+// For n > 12, polymul reads the column-transformed a (in c) and b (in the
+// scratch s) and leaves lazy c' rows for k_col_inv.
+template <int MODE>
+__global__ void __launch_bounds__(256, 2) k_rows(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  const uint32_t logn = P.logn;
+  const uint32_t rows_per_unit = 1u << (logn - kRowLog);
+  const uint32_t unit = blockIdx.x >> (logn - kRowLog);
+  const uint32_t t = blockIdx.x & (rows_per_unit - 1);
+  if (unit >= P.nunits) return;  // whole CTA exits together
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twf = P.twf + ((size_t)limb << logn);
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
+  RowIO io;
+  io.sa = smem;
+  io.sb = smem + kRowPad;
+  const bool single = (logn == kRowLog);
+  if (MODE == MODE_POLYMUL) {
+    io.ga = (single ? P.a : P.c) + off;
+    io.gb = (single ? P.b : P.s) + off;
+    io.gc = P.c + off;
+    if (single)
+      row_pipeline<MODE_POLYMUL, false, false, true>(io, twf, twi, K, logn, t, threadIdx.x);
+    else
+      row_pipeline<MODE_POLYMUL, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
+  } else if (MODE == MODE_FWD) {
+    io.ga = P.c + off;
+    io.gb = nullptr;
+    io.gc = P.c + off;
+    row_pipeline<MODE_FWD, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
+  } else {
+    io.ga = P.c + off;
+    io.gb = nullptr;
+    io.gc = P.c + off;
+    if (single)
+      row_pipeline<MODE_INV, false, false, true>(io, twf, twi, K, logn, t, threadIdx.x);
+    else
+      row_pipeline<MODE_INV, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
+  }
+}
+
+// Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
+// operand, column); loads the R words {c + 4096 t}, runs the first log2 R
+// stages of Algorithm 6, stores them back in place (to `dst`).
+// For polymul, operand 0 (a) goes to c and operand 1 (b) to the scratch s.
+template <int R>
+__global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+  const uint32_t logn = P.logn;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t col = (uint32_t)(gid & (kRow - 1));
+  const size_t rest = gid >> kRowLog;
+  const uint32_t op = (uint32_t)(rest % nops);
+  const uint32_t unit = (uint32_t)(rest / nops);
+  if (unit >= P.nunits) return;
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twf = P.twf + ((size_t)limb << logn);
+  const size_t off = ((size_t)unit << logn) + col;
+  const uint64_t* src = (op == 0 ? P.a : P.b) + off;
+  uint64_t* dst = (op == 0 ? P.c : P.s) + off;
+  uint64_t x[R];
+#pragma unroll
+  for (int t = 0; t < R; t++) x[t] = __ldcs(src + (size_t)t * kRow);
+  ct_col<R>(x, twf, K.q, K.two_q);
+#pragma unroll
+  for (int t = 0; t < R; t++) dst[(size_t)t * kRow] = x[t];
+}
+
+// Inverse column stages (the last log2 R stages of Algorithm 7, 1/2-scaled)
+// plus the reduction to [0, q); in place on c.
+template <int R>
+__global__ void __launch_bounds__(256) k_col_inv(KParams P) {
+  const uint32_t logn = P.logn;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t col = (uint32_t)(gid & (kRow - 1));
+  const uint32_t unit = (uint32_t)(gid >> kRowLog);
+  if (unit >= P.nunits) return;
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  uint64_t* p = P.c + ((size_t)unit << logn) + col;
+  uint64_t x[R];
+#pragma unroll
+  for (int t = 0; t < R; t++) x[t] = p[(size_t)t * kRow];
+  gs_col<R>(x, twi, K.q, K.two_q, K.half_q1);
+#pragma unroll
+  for (int t = 0; t < R; t++) __stcs(p + (size_t)t * kRow, csub(x[t], K.q));
+}
+
+// N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
+// (k = 4096) runs between global memory and smem; rows as in k_rows.
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  constexpr uint32_t logn = 13;
+  const uint32_t unit = blockIdx.x;
+  if (unit >= P.nunits) return;
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twf = P.twf + ((size_t)limb << logn);
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const int tid = threadIdx.x;
+  const int rho = tid >> 8, th = tid & 255;
+  // smem: [a row0][a row1][b row0][b row1]
+  uint64_t* sA = smem;
+  uint64_t* sB = smem + 2 * kRowPad;
+  const size_t base = (size_t)unit << logn;
+  RowIO io;
+  io.sa = sA + rho * kRowPad;
+  io.sb = sB + rho * kRowPad;
+  io.ga = io.gb = nullptr;
+  io.gc = P.c + base + (size_t)rho * kRow;
+  if (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
+    const int nops = (MODE == MODE_POLYMUL) ? 2 : 1;
+    const TwPair w = ld_tw(twf + 1);
+    for (int op = 0; op < nops; op++) {
+      const uint64_t* src = (MODE == MODE_FWD) ? P.c + base : (op == 0 ? P.a : P.b) + base;
+      uint64_t* dsm = op == 0 ? sA : sB;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const int c = tid + 512 * k;
+        uint64_t x0 = __ldcs(src + c), x1 = __ldcs(src + kRow + c);
+        ct_bfly(x0, x1, w.w, w.wp, K.q, K.two_q);
+        dsm[padj(c)] = x0;
+        dsm[kRowPad + padj(c)] = x1;
+      }
+    }
+    __syncthreads();
+    if constexpr (MODE == MODE_FWD) {
+      row_pipeline<MODE_FWD, true, false, false>(io, twf, twi, K, logn, rho, th);
+      return;
+    }
+    row_pipeline<MODE_POLYMUL, true, true, false>(io, twf, twi, K, logn, rho, th);
+  } else {
+    io.ga = P.c + base + (size_t)rho * kRow;
+    row_pipeline<MODE_INV, false, true, false>(io, twf, twi, K, logn, rho, th);
+  }
+  __syncthreads();
+  // last GS stage (k = 4096), twiddle Psi^-1_br[1] (times 1/2), then reduce
+  const TwPair w = ld_tw(twi + 1);
+  uint64_t* dst = P.c + base;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const int c = tid + 512 * k;
+    uint64_t x0 = sA[padj(c)], x1 = sA[kRowPad + padj(c)];
+    gs_bfly_half(x0, x1, w.w, w.wp, K.q, K.two_q, K.half_q1);
+    __stcs(dst + c, csub(x0, K.q));
+    __stcs(dst + kRow + c, csub(x1, K.q));
+  }
+}
+
+// N <= 2^11: one CTA per unit, Algorithms 6 and 7 stage by stage in smem.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_small(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  const uint32_t logn = P.logn, n = 1u << logn;
+  const uint32_t unit = blockIdx.x;
+  if (unit >= P.nunits) return;
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twf = P.twf + ((size_t)limb << logn);
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const size_t base = (size_t)unit << logn;
+  uint64_t* xa = smem;
+  uint64_t* xb = smem + n;
+  const uint64_t q = K.q, two_q = K.two_q;
+  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
+    const int nops = (MODE == MODE_POLYMUL) ? 2 : 1;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      xa[i] = (MODE == MODE_FWD) ? P.c[base + i] : P.a[base + i];
+      if (nops == 2) xb[i] = P.b[base + i];
+    }
+    __syncthreads();
+    for (uint32_t m = 1, k = n >> 1; m < n; m <<= 1, k >>= 1) {
+      for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
+        const uint32_t i = b / k, j = 2 * i * k + (b % k);
+        const TwPair w = ld_tw(twf + m + i);
+        ct_bfly(xa[j], xa[j + k], w.w, w.wp, q, two_q);
+        if (nops == 2) ct_bfly(xb[j], xb[j + k], w.w, w.wp, q, two_q);
+      }
+      __syncthreads();
+    }
+    if constexpr (MODE == MODE_FWD) {
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P.c[base + i] = reduce4(xa[i], q, two_q);
+      return;
+    }
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+      xa[i] = mul_barrett_alg4(reduce4(xa[i], q, two_q), reduce4(xb[i], q, two_q), K);
+  } else {
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) xa[i] = P.c[base + i];
+  }
+  __syncthreads();
+  for (uint32_t m = n >> 1, k = 1; m >= 1; m >>= 1, k <<= 1) {
+    for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const uint32_t i = b / k, j = 2 * i * k + (b % k);
+      const TwPair w = ld_tw(twi + m + i);
+      gs_bfly_half(xa[j], xa[j + k], w.w, w.wp, q, two_q, K.half_q1);
+    }
+    __syncthreads();
+  }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P.c[base + i] = csub(xa[i], q);
+}
+
+// Stand-alone pointwise product, Algorithm 4, two words per thread.
+__global__ void __launch_bounds__(256) k_pointwise(KParams P) {
+  const size_t total = (size_t)P.nunits << P.logn;
+  const size_t stride = (size_t)gridDim.x * blockDim.x * 2;
+  for (size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < total; i += stride) {
+    const uint32_t limb = (uint32_t)((i >> P.logn) % P.nlimbs);
+    const LimbConst K = ld_limb(P.lc + limb);
+    if (i + 1 < total && ((i + 1) >> P.logn) == (i >> P.logn)) {
+      const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(P.a + i);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(P.b + i);
+      *reinterpret_cast<ulonglong2*>(P.c + i) =
+          make_ulonglong2(mul_barrett_alg4(a.x, b.x, K), mul_barrett_alg4(a.y, b.y, K));
+    } else {
+      for (size_t k = i; k < i + 2 && k < total; k++) {
+        const LimbConst K2 = ld_limb(P.lc + (uint32_t)((k >> P.logn) % P.nlimbs));
+        P.c[k] = mul_barrett_alg4(P.a[k], P.b[k], K2);
+      }
+    }
+  }
+}
+
+// Range check 0 <= x < q_l; sets *flag = 1 on any violation.
+__global__ void __launch_bounds__(256) k_check_reduced(KParams P, int* flag) {
+  const size_t total = (size_t)P.nunits << P.logn;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t limb = (uint32_t)((i >> P.logn) % P.nlimbs);
+    if (P.a[i] >= __ldg(&P.lc[limb].q)) atomicOr(flag, 1);
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+static cudaError_t set_smem(const void* fn, int bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int R>
+static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
+  const size_t threads = (size_t)P.nunits * nops * kRow;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  k_col_fwd<R><<<blocks, 256, 0, st>>>(P, nops);
+  return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
+  const size_t threads = (size_t)P.nunits * kRow;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  k_col_inv<R><<<blocks, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+static cudaError_t col_fwd(const KParams& P, int nops, cudaStream_t st) {
+  switch (P.logn) {
+    case 13: return launch_col_fwd<2>(P, nops, st);
+    case 14: return launch_col_fwd<4>(P, nops, st);
+    case 15: return launch_col_fwd<8>(P, nops, st);
+    case 16: return launch_col_fwd<16>(P, nops, st);
+    case 17: return launch_col_fwd<32>(P, nops, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t col_inv(const KParams& P, cudaStream_t st) {
+  switch (P.logn) {
+    case 13: return launch_col_inv<2>(P, st);
+    case 14: return launch_col_inv<4>(P, st);
+    case 15: return launch_col_inv<8>(P, st);
+    case 16: return launch_col_inv<16>(P, st);
+    case 17: return launch_col_inv<32>(P, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+constexpr int kRowsSmem = 2 * kRowPad * 8;
+constexpr int kFused13Smem = 4 * kRowPad * 8;
+
+template <int MODE>
+static cudaError_t rows(const KParams& P, cudaStream_t st) {
+  const int smem = kRowsSmem;
+  const unsigned blocks = P.nunits << (P.logn - kRowLog);
+  k_rows<MODE><<<blocks, 256, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t fused13(const KParams& P, cudaStream_t st) {
+  const int smem = kFused13Smem;
+  k_fused13<MODE><<<P.nunits, 512, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t small(const KParams& P, cudaStream_t st) {
+  const int smem = 2 * (1 << P.logn) * 8;
+  k_small<MODE><<<P.nunits, 256, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+// Opt the large-smem kernels in to their dynamic shared memory on the current
+// device (once per device, before the first launch).
+cudaError_t kernels_prepare() {
+  cudaError_t e;
+  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows<MODE_FWD>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows<MODE_INV>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL>, kFused13Smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_FWD>, kFused13Smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_INV>, kFused13Smem)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+static inline cudaError_t mark(const PhaseEvents* pe, int k, cudaStream_t st) {
+  return (pe && k < pe->n) ? cudaEventRecord(pe->ev[k], st) : cudaSuccess;
+}
+
+cudaError_t launch_polymul(const KParams& P0, cudaStream_t st, const PhaseEvents* pe) {
+  KParams P = P0;
+  if (P.nunits == 0) return cudaSuccess;
+  cudaError_t e0 = mark(pe, 0, st);
+  if (e0 != cudaSuccess) return e0;
+  if (P.logn <= 13) {
+    e0 = P.logn <= 11 ? small<MODE_POLYMUL>(P, st)
+                      : (P.logn == 12 ? rows<MODE_POLYMUL>(P, st) : fused13<MODE_POLYMUL>(P, st));
+    if (e0 != cudaSuccess) return e0;
+    return mark(pe, 1, st);
+  }
+  // Column stages of a and b: one operand goes to c, the other to the
+  // scratch s; the row kernel reads (c, s) in either order since the
+  // pointwise product commutes.  Each column thread reads its own words
+  // before writing them, so c may alias the operand whose image it receives.
+  int nops = 2;
+  if (P.a == P.b) {
+    P.b = nullptr;
+    P.s = P.c;  // square: one transform, read twice
+    nops = 1;
+  } else if (P.c == P.b) {
+    const uint64_t* t = P.a;  // b's image stays in place, a's goes to s
+    P.a = P.b;
+    P.b = t;
+  }
+  cudaError_t e = col_fwd(P, nops, st);
+  if (e == cudaSuccess) e = mark(pe, 1, st);
+  if (e == cudaSuccess) e = rows<MODE_POLYMUL>(P, st);
+  if (e == cudaSuccess) e = mark(pe, 2, st);
+  if (e == cudaSuccess) e = col_inv(P, st);
+  if (e == cudaSuccess) e = mark(pe, 3, st);
+  return e;
+}
+
+cudaError_t launch_ntt_fwd(const KParams& P0, cudaStream_t st) {
+  if (P0.nunits == 0) return cudaSuccess;
+  KParams P = P0;
+  if (P.logn <= 11) return small<MODE_FWD>(P, st);
+  if (P.logn == 13) return fused13<MODE_FWD>(P, st);
+  if (P.logn > 13) {
+    P.a = P.c;  // in place: column stages read and write x
+    cudaError_t e = col_fwd(P, 1, st);
+    if (e != cudaSuccess) return e;
+  }
+  return rows<MODE_FWD>(P, st);
+}
+
+cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st) {
+  if (P.nunits == 0) return cudaSuccess;
+  if (P.logn <= 11) return small<MODE_INV>(P, st);
+  if (P.logn == 13) return fused13<MODE_INV>(P, st);
+  cudaError_t e = rows<MODE_INV>(P, st);
+  if (e != cudaSuccess || P.logn == 12) return e;
+  return col_inv(P, st);
+}
+
+cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms) {
+  const size_t total = (size_t)P.nunits << P.logn;
+  if (total == 0) return cudaSuccess;
+  size_t blocks = (total / 2 + 255) / 256;
+  const size_t cap = (size_t)num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_pointwise<<<(unsigned)blocks, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st, int num_sms) {
+  const size_t total = (size_t)P.nunits << P.logn;
+  if (total == 0) return cudaSuccess;
+  size_t blocks = (total + 255) / 256;
+  const size_t cap = (size_t)num_sms * 8;
+  if (blocks > cap) blocks = cap;
+  k_check_reduced<<<(unsigned)blocks, 256, 0, st>>>(P, d_flag);
+  return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -1,0 +1,23 @@
+// pm_params.h -- host-side number theory and table construction for plans.
+#pragma once
+#include <cstdint>
+
+#include "pm_types.h"
+
+namespace pm {
+namespace host {
+
+uint64_t pow_mod(uint64_t base, uint64_t exp, uint64_t q);
+bool is_prime_u64(uint64_t n);
+uint32_t bit_length(uint64_t x);
+// The `count` largest primes q < 2^qbits with q = 1 (mod 2N), descending.
+// Returns how many were found.
+int largest_ntt_primes(uint32_t log2n, uint32_t qbits, uint32_t count, uint64_t* out);
+// psi for q by the fixed search rule; 0 if q is not = 1 mod 2N or none found.
+uint64_t default_psi(uint64_t q, uint32_t log2n);
+// Limb constants and twiddle tables (host arrays of N entries).
+void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, LimbConst* lc, TwPair* twf,
+                TwPair* twi);
+
+}  // namespace host
+}  // namespace pm

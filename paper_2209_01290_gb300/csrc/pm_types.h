@@ -1,0 +1,26 @@
+// pm_types.h -- plain data shared by host and device code.
+#pragma once
+#include <cstdint>
+
+namespace pm {
+
+// Per-limb constants, 64 bytes, read through the read-only path.
+struct alignas(64) LimbConst {
+  uint64_t q;        // modulus
+  uint64_t two_q;    // 2q
+  uint64_t half_q1;  // (q + 1) / 2: the odd-case addend of x/2 mod q (Sec. III-A)
+  uint64_t mu;       // Algorithm 4: floor(2^(2m+1) / q)
+  uint32_t m;        // len(q), bit length
+  uint32_t sh1;      // m - 2   (Algorithm 4, step 1 shift)
+  uint32_t sh2;      // m + 3   (Algorithm 4, step 2 shift)
+  uint32_t pad0;
+  uint64_t pad1[3];
+};
+
+// Twiddle factor with its Shoup companion floor(w * 2^64 / q), 16 bytes.
+struct alignas(16) TwPair {
+  uint64_t w;
+  uint64_t wp;
+};
+
+}  // namespace pm
