@@ -215,6 +215,9 @@ def run_gpu(args):
     nphase = 4 if log2n >= 14 else 2
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nphase)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for e in [x for row in ev for x in row] + [start, end]:
+        e.record(stream)  # torch creates the CUDA event on first record
+    stream.synchronize()
     sampler = ClockSampler(dev)
     if dist is not None:
         dist.barrier()
