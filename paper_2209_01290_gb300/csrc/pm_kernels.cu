@@ -50,30 +50,26 @@ __device__ __forceinline__ int padj(int j) { return j + (j >> 5); }
 // number g, its 16 words spaced N >> (s0+4) apart.  Stage s0+st pairs
 // (u, u + 8 >> st) with twiddle Psi_br[2^(s0+st) + g 2^st + (u >> (4-st))].
 // (Stages are template parameters so every register index is a constant.)
-template <int ST, int NOPS>
-__device__ __forceinline__ void ct16_stage(uint64_t (&v)[2][16], const TwPair* __restrict__ tw,
-                                           uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
+template <int ST>
+__device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __restrict__ tw,
+                                            uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
   constexpr int h = 8 >> ST;
   const uint32_t base = (1u << (s0 + ST)) + (g << ST);
 #pragma unroll
   for (int blk = 0; blk < (1 << ST); blk++) {
     const TwPair t = ld_tw(tw + base + blk);
 #pragma unroll
-    for (int u0 = 0; u0 < h; u0++) {
-#pragma unroll
-      for (int o = 0; o < NOPS; o++)
-        ct_bfly(v[o][blk * 2 * h + u0], v[o][blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
-    }
+    for (int u0 = 0; u0 < h; u0++)
+      ct_bfly(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
   }
 }
 
-template <int NOPS>
-__device__ __forceinline__ void ct16(uint64_t (&v)[2][16], const TwPair* __restrict__ tw,
+__device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                      uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
-  ct16_stage<0, NOPS>(v, tw, s0, g, q, two_q);
-  ct16_stage<1, NOPS>(v, tw, s0, g, q, two_q);
-  ct16_stage<2, NOPS>(v, tw, s0, g, q, two_q);
-  ct16_stage<3, NOPS>(v, tw, s0, g, q, two_q);
+  ct16_stage1<0>(v, tw, s0, g, q, two_q);
+  ct16_stage1<1>(v, tw, s0, g, q, two_q);
+  ct16_stage1<2>(v, tw, s0, g, q, two_q);
+  ct16_stage1<3>(v, tw, s0, g, q, two_q);
 }
 
 // Four consecutive merged-GS stages (Algorithm 7, 1/2-scaled) on a group of
@@ -170,176 +166,152 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
 
 // ----------------------------------------------------------- row pipeline
 
-// Register/smem pipeline for the 12 in-row stages of one 4096-word row (row
-// t of a unit of 2^logn words).  256 threads per row; thread th owns
-//   pass A (P0 / Q2): words th + 256 u            (u = 0..15)
-//   pass B (P1 / Q1): words 256 (th>>4) + (th&15) + 16 u
-//   pass C (P2 / Q0): words 16 th + u
-// which are all bank-conflict free with the 1-in-32 padding.
-struct RowIO {
-  const uint64_t* ga;  // global row of operand a (pass A source), or null
-  const uint64_t* gb;  // global row of operand b
-  uint64_t* gc;        // global row of the output
-  uint64_t* sa;        // smem row buffer, operand a / result
-  uint64_t* sb;        // smem row buffer, operand b
+// The 12 in-row stages of one 4096-word row (row t of a unit of 2^logn
+// words) as three radix-16 passes; 256 threads per row.  Each pass reads 16
+// words per thread, runs 4 stages in registers and writes them back.  The
+// three thread->word layouts
+//   layout 0: j = th + 256 u                      (CT stages n-12.., GS 8..11)
+//   layout 1: j = 256 (th>>4) + (th&15) + 16 u    (CT stages n-8..,  GS 4..7)
+//   layout 2: j = 16 th + u                       (CT stages n-4..,  GS 0..3)
+// are all bank-conflict free with the 1-in-32 padding.  The pass loop is
+// not unrolled: one copy of the radix-16 body serves all passes, which keeps
+// the kernel small enough for the instruction cache.
+struct PassGeo {
+  int base;      // word index of u = 0
+  int stride;    // word distance between u and u + 1
+  uint32_t g;    // block index of the group within the whole transform
 };
 
-// MODE_FWD: rows of x -> P0..P2 -> canonical bo-order row (global, pass C
-// layout).  MODE_INV: x rows -> Q0..Q2 -> output.  MODE_POLYMUL: a, b rows ->
-// P0..P2 -> Barrett -> Q0..Q2 -> output.
-// SRC_SMEM: P0 (or Q0 for INV) reads the smem buffers instead of global.
-// DST_SMEM: Q2 writes the smem buffer instead of global (lazy [0,2q) kept);
-// otherwise Q2 writes global, canonical if FINAL else lazy.
-template <int MODE, bool SRC_SMEM, bool DST_SMEM, bool FINAL>
-__device__ __forceinline__ void row_pipeline(const RowIO& io, const TwPair* __restrict__ twf,
-                                             const TwPair* __restrict__ twi,
-                                             const LimbConst& K, uint32_t logn, uint32_t t,
-                                             int th) {
-  const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
-  uint64_t v[2][16];
-  const int g1 = th >> 4, o1 = th & 15;
-  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
-    constexpr int NOPS = (MODE == MODE_POLYMUL) ? 2 : 1;
-    // ---- P0: CT stages n-12 .. n-9, pass A layout
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int j = th + 256 * u;
-      if (SRC_SMEM) {
-        v[0][u] = io.sa[padj(j)];
-        if (NOPS == 2) v[1][u] = io.sb[padj(j)];
-      } else {
-        v[0][u] = __ldcs(io.ga + j);
-        if (NOPS == 2) v[1][u] = __ldcs(io.gb + j);
-      }
-    }
-    ct16<NOPS>(v, twf, logn - 12, t, q, two_q);
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int j = padj(th + 256 * u);
-      io.sa[j] = v[0][u];
-      if (NOPS == 2) io.sb[j] = v[1][u];
-    }
-    __syncthreads();
-    // ---- P1: CT stages n-8 .. n-5, pass B layout
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int j = padj(256 * g1 + o1 + 16 * u);
-      v[0][u] = io.sa[j];
-      if (NOPS == 2) v[1][u] = io.sb[j];
-    }
-    ct16<NOPS>(v, twf, logn - 8, t * 16 + g1, q, two_q);
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int j = padj(256 * g1 + o1 + 16 * u);
-      io.sa[j] = v[0][u];
-      if (NOPS == 2) io.sb[j] = v[1][u];
-    }
-    __syncthreads();
-    // ---- P2: CT stages n-4 .. n-1, pass C layout
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int j = padj(16 * th + u);
-      v[0][u] = io.sa[j];
-      if (NOPS == 2) v[1][u] = io.sb[j];
-    }
-    ct16<NOPS>(v, twf, logn - 4, t * 256 + th, q, two_q);
-    if constexpr (MODE == MODE_FWD) {
-      ulonglong2* dst = reinterpret_cast<ulonglong2*>(io.gc + 16 * th);
-#pragma unroll
-      for (int u = 0; u < 16; u += 2)
-        __stcs(dst + u / 2, make_ulonglong2(reduce4(v[0][u], q, two_q),
-                                            reduce4(v[0][u + 1], q, two_q)));
-      return;
-    }
-    // ---- pointwise product (Algorithm 4), bit-reversed order
-#pragma unroll
-    for (int u = 0; u < 16; u++)
-      v[0][u] = mul_barrett_alg4(reduce4(v[0][u], q, two_q), reduce4(v[1][u], q, two_q), K);
+__device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
+  PassGeo G;
+  if (layout == 0) {
+    G.base = th;
+    G.stride = 256;
+    G.g = t;
+  } else if (layout == 1) {
+    G.base = 256 * (th >> 4) + (th & 15);
+    G.stride = 16;
+    G.g = t * 16 + (th >> 4);
   } else {
-    // MODE_INV: Q0 input in pass C layout
-    if (SRC_SMEM) {
+    G.base = 16 * th;
+    G.stride = 1;
+    G.g = t * 256 + th;
+  }
+  return G;
+}
+
+__device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
 #pragma unroll
-      for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(16 * th + u)];
+  for (int u = 0; u < 16; u++) v[u] = s[padj(G.base + G.stride * u)];
+}
+
+__device__ __forceinline__ void st_smem16(uint64_t* s, const PassGeo& G, const uint64_t (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 16; u++) s[padj(G.base + G.stride * u)] = v[u];
+}
+
+// Forward in-row stages of one operand.  Source: global row `g_src` (layout
+// 0, coalesced) or, if null, the smem row `s` (already holding the row).
+// Leaves the last pass's 16 words (layout 2, lazy [0,4q)) in v.
+__device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_src, uint64_t* s,
+                                         const TwPair* __restrict__ twf, uint32_t logn,
+                                         uint32_t t, int th, uint64_t q, uint64_t two_q) {
+#pragma unroll 1
+  for (int p = 0; p < 3; p++) {
+    const PassGeo G = pass_geo(p, th, t);
+    if (p == 0 && g_src) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) v[u] = __ldcs(g_src + th + 256 * u);
     } else {
-      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(io.ga + 16 * th);
-#pragma unroll
-      for (int u = 0; u < 16; u += 2) {
-        const ulonglong2 w = __ldcs(src + u / 2);
-        v[0][u] = w.x;
-        v[0][u + 1] = w.y;
-      }
+      ld_smem16(v, s, G);
+    }
+    ct16(v, twf, logn - 12 + 4 * p, G.g, q, two_q);
+    if (p < 2) {
+      st_smem16(s, G, v);
+      __syncthreads();
     }
   }
-  // ---- Q0: GS stages 0..3 (k = 1..8), pass C layout
-  gs16(v[0], twi, logn, 0, t * 256 + th, q, two_q, hq);
+}
+
+// Inverse in-row stages (1/2-scaled).  v holds layout-2 words on entry.
+// The last pass writes layout 0 either to the global row `g_dst`
+// (canonical if `final`) or, if null, back to smem.
+__device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, bool final,
+                                         uint64_t* s, const TwPair* __restrict__ twi,
+                                         uint32_t logn, uint32_t t, int th, uint64_t q,
+                                         uint64_t two_q, uint64_t hq) {
+#pragma unroll 1
+  for (int p = 0; p < 3; p++) {
+    const PassGeo G = pass_geo(2 - p, th, t);
+    if (p > 0) ld_smem16(v, s, G);
+    gs16(v, twi, logn, 4 * p, G.g, q, two_q, hq);
+    if (p < 2) {
+      st_smem16(s, G, v);
+      __syncthreads();
+    }
+  }
+  if (g_dst) {
 #pragma unroll
-  for (int u = 0; u < 16; u++) io.sa[padj(16 * th + u)] = v[0][u];
-  __syncthreads();
-  // ---- Q1: GS stages 4..7, pass B layout
-#pragma unroll
-  for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(256 * g1 + o1 + 16 * u)];
-  gs16(v[0], twi, logn, 4, t * 16 + g1, q, two_q, hq);
-#pragma unroll
-  for (int u = 0; u < 16; u++) io.sa[padj(256 * g1 + o1 + 16 * u)] = v[0][u];
-  __syncthreads();
-  // ---- Q2: GS stages 8..11, pass A layout
-#pragma unroll
-  for (int u = 0; u < 16; u++) v[0][u] = io.sa[padj(th + 256 * u)];
-  gs16(v[0], twi, logn, 8, t, q, two_q, hq);
-  if constexpr (DST_SMEM) {
-#pragma unroll
-    for (int u = 0; u < 16; u++) io.sa[padj(th + 256 * u)] = v[0][u];
+    for (int u = 0; u < 16; u++) __stcs(g_dst + th + 256 * u, final ? csub(v[u], q) : v[u]);
   } else {
-#pragma unroll
-    for (int u = 0; u < 16; u++)
-      __stcs(io.gc + th + 256 * u, FINAL ? csub(v[0][u], q) : v[0][u]);
+    st_smem16(s, pass_geo(0, th, t), v);
   }
 }
 
 // ------------------------------------------------------------------ kernels
 
 // In-row stages for n >= 12.  One CTA = one row (256 threads).  For n == 12
-// the row is the whole unit (MODE_POLYMUL reads a, b; output canonical).
-// For n > 12, polymul reads the column-transformed a (in c) and b (in the
-// scratch s) and leaves lazy c' rows for k_col_inv.
+// the row is the whole unit (polymul reads a, b; output canonical).  For
+// n > 12, polymul reads the column-transformed operands from c and the
+// scratch s and leaves lazy c' rows for k_col_inv.
 template <int MODE>
-__global__ void __launch_bounds__(256, 2) k_rows(KParams P) {
+__global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
   extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t logn = P.logn;
-  const uint32_t rows_per_unit = 1u << (logn - kRowLog);
   const uint32_t unit = blockIdx.x >> (logn - kRowLog);
-  const uint32_t t = blockIdx.x & (rows_per_unit - 1);
+  const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
   if (unit >= P.nunits) return;  // whole CTA exits together
   const uint32_t limb = unit % P.nlimbs;
   const LimbConst K = ld_limb(P.lc + limb);
   const TwPair* twf = P.twf + ((size_t)limb << logn);
   const TwPair* twi = P.twi + ((size_t)limb << logn);
   const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
-  RowIO io;
-  io.sa = smem;
-  io.sb = smem + kRowPad;
   const bool single = (logn == kRowLog);
-  if (MODE == MODE_POLYMUL) {
-    io.ga = (single ? P.a : P.c) + off;
-    io.gb = (single ? P.b : P.s) + off;
-    io.gc = P.c + off;
-    if (single)
-      row_pipeline<MODE_POLYMUL, false, false, true>(io, twf, twi, K, logn, t, threadIdx.x);
-    else
-      row_pipeline<MODE_POLYMUL, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
-  } else if (MODE == MODE_FWD) {
-    io.ga = P.c + off;
-    io.gb = nullptr;
-    io.gc = P.c + off;
-    row_pipeline<MODE_FWD, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
+  const int th = threadIdx.x;
+  uint64_t* sa = smem;
+  uint64_t* sb = smem + kRowPad;
+  uint64_t v[16];
+  if constexpr (MODE == MODE_INV) {
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(P.c + off + 16 * th);
+#pragma unroll
+    for (int u = 0; u < 16; u += 2) {
+      const ulonglong2 w = __ldcs(src + u / 2);
+      v[u] = w.x;
+      v[u + 1] = w.y;
+    }
+    rows_inv(v, P.c + off, single, sa, twi, logn, t, th, K.q, K.two_q, K.half_q1);
+  } else if constexpr (MODE == MODE_FWD) {
+    rows_fwd(v, P.c + off, sa, twf, logn, t, th, K.q, K.two_q);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + off + 16 * th);
+#pragma unroll
+    for (int u = 0; u < 16; u += 2)
+      __stcs(dst + u / 2, make_ulonglong2(reduce4(v[u], K.q, K.two_q),
+                                          reduce4(v[u + 1], K.q, K.two_q)));
   } else {
-    io.ga = P.c + off;
-    io.gb = nullptr;
-    io.gc = P.c + off;
-    if (single)
-      row_pipeline<MODE_INV, false, false, true>(io, twf, twi, K, logn, t, threadIdx.x);
-    else
-      row_pipeline<MODE_INV, false, false, false>(io, twf, twi, K, logn, t, threadIdx.x);
+    const uint64_t* ga = (single ? P.a : P.c) + off;
+    const uint64_t* gb = (single ? P.b : P.s) + off;
+    // operand a: keep its transform in smem (layout 2) while b is done
+    rows_fwd(v, ga, sa, twf, logn, t, th, K.q, K.two_q);
+    const PassGeo G2 = pass_geo(2, th, t);
+    st_smem16(sa, G2, v);
+    rows_fwd(v, gb, sb, twf, logn, t, th, K.q, K.two_q);
+    // pointwise product (Algorithm 4) in bit-reversed order
+#pragma unroll
+    for (int u = 0; u < 16; u++) {
+      const uint64_t ahat = reduce4(sa[padj(G2.base + u)], K.q, K.two_q);
+      v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
+    }
+    rows_inv(v, P.c + off, single, sa, twi, logn, t, th, K.q, K.two_q, K.half_q1);
   }
 }
 
@@ -408,13 +380,11 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
   // smem: [a row0][a row1][b row0][b row1]
   uint64_t* sA = smem;
   uint64_t* sB = smem + 2 * kRowPad;
+  uint64_t* sa = sA + rho * kRowPad;
+  uint64_t* sb = sB + rho * kRowPad;
   const size_t base = (size_t)unit << logn;
-  RowIO io;
-  io.sa = sA + rho * kRowPad;
-  io.sb = sB + rho * kRowPad;
-  io.ga = io.gb = nullptr;
-  io.gc = P.c + base + (size_t)rho * kRow;
-  if (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
+  uint64_t v[16];
+  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
     const int nops = (MODE == MODE_POLYMUL) ? 2 : 1;
     const TwPair w = ld_tw(twf + 1);
     for (int op = 0; op < nops; op++) {
@@ -430,15 +400,35 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       }
     }
     __syncthreads();
+    rows_fwd(v, nullptr, sa, twf, logn, rho, th, K.q, K.two_q);
     if constexpr (MODE == MODE_FWD) {
-      row_pipeline<MODE_FWD, true, false, false>(io, twf, twi, K, logn, rho, th);
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + base + (size_t)rho * kRow + 16 * th);
+#pragma unroll
+      for (int u = 0; u < 16; u += 2)
+        __stcs(dst + u / 2, make_ulonglong2(reduce4(v[u], K.q, K.two_q),
+                                            reduce4(v[u + 1], K.q, K.two_q)));
       return;
+    } else {
+      const PassGeo G2 = pass_geo(2, th, rho);
+      st_smem16(sa, G2, v);
+      rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q);
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        const uint64_t ahat = reduce4(sa[padj(G2.base + u)], K.q, K.two_q);
+        v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
+      }
     }
-    row_pipeline<MODE_POLYMUL, true, true, false>(io, twf, twi, K, logn, rho, th);
   } else {
-    io.ga = P.c + base + (size_t)rho * kRow;
-    row_pipeline<MODE_INV, false, true, false>(io, twf, twi, K, logn, rho, th);
+    const ulonglong2* src =
+        reinterpret_cast<const ulonglong2*>(P.c + base + (size_t)rho * kRow + 16 * th);
+#pragma unroll
+    for (int u = 0; u < 16; u += 2) {
+      const ulonglong2 w = __ldcs(src + u / 2);
+      v[u] = w.x;
+      v[u + 1] = w.y;
+    }
   }
+  rows_inv(v, nullptr, false, sa, twi, logn, rho, th, K.q, K.two_q, K.half_q1);
   __syncthreads();
   // last GS stage (k = 4096), twiddle Psi^-1_br[1] (times 1/2), then reduce
   const TwPair w = ld_tw(twi + 1);
