@@ -19,11 +19,13 @@ __device__ __forceinline__ TwPair ld_tw(const TwPair* __restrict__ p) {
 }
 
 // w * y mod q up to one multiple of q (Shoup): for w < q and any 64-bit y,
-// the result is congruent to w*y and lies in [0, 2q).
+// the result is congruent to w*y and lies in [0, 2q).  Written as
+// w*y + qh*(2^64 - q) mod 2^64 so that the subtraction folds into the
+// multiply-add chain of the low-word products.
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint64_t wp,
                                                    uint64_t q) {
   const uint64_t qh = __umul64hi(wp, y);
-  return w * y - qh * q;
+  return w * y + qh * (0 - q);
 }
 
 __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }

@@ -177,37 +177,59 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
 // not unrolled: one copy of the radix-16 body serves all passes, which keeps
 // the kernel small enough for the instruction cache.
 struct PassGeo {
-  int base;      // word index of u = 0
-  int stride;    // word distance between u and u + 1
+  int layout;    // 0, 1 or 2
+  int pbase;     // padded smem index of u = 0
   uint32_t g;    // block index of the group within the whole transform
 };
 
+// With the 1-in-32 padding p(j) = j + (j >> 5), the padded index of word u
+// of a group is pbase + off(u) with a compile-time offset per layout:
+//   layout 0: 264 u;  layout 1: 16 u + (u >> 1);  layout 2: u.
+template <int L>
+__device__ __forceinline__ constexpr int lay_off(int u) {
+  return L == 0 ? 264 * u : (L == 1 ? 16 * u + (u >> 1) : u);
+}
+
 __device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
   PassGeo G;
+  G.layout = layout;
   if (layout == 0) {
-    G.base = th;
-    G.stride = 256;
+    G.pbase = th + (th >> 5);
     G.g = t;
   } else if (layout == 1) {
-    G.base = 256 * (th >> 4) + (th & 15);
-    G.stride = 16;
+    G.pbase = 264 * (th >> 4) + (th & 15);
     G.g = t * 16 + (th >> 4);
   } else {
-    G.base = 16 * th;
-    G.stride = 1;
+    G.pbase = 16 * th + (th >> 1);
     G.g = t * 256 + th;
   }
   return G;
 }
 
-__device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
+template <int L>
+__device__ __forceinline__ void ld16(uint64_t (&v)[16], const uint64_t* s) {
 #pragma unroll
-  for (int u = 0; u < 16; u++) v[u] = s[padj(G.base + G.stride * u)];
+  for (int u = 0; u < 16; u++) v[u] = s[lay_off<L>(u)];
+}
+
+template <int L>
+__device__ __forceinline__ void st16(uint64_t* s, const uint64_t (&v)[16]) {
+#pragma unroll
+  for (int u = 0; u < 16; u++) s[lay_off<L>(u)] = v[u];
+}
+
+__device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
+  const uint64_t* p = s + G.pbase;
+  if (G.layout == 0) ld16<0>(v, p);
+  else if (G.layout == 1) ld16<1>(v, p);
+  else ld16<2>(v, p);
 }
 
 __device__ __forceinline__ void st_smem16(uint64_t* s, const PassGeo& G, const uint64_t (&v)[16]) {
-#pragma unroll
-  for (int u = 0; u < 16; u++) s[padj(G.base + G.stride * u)] = v[u];
+  uint64_t* p = s + G.pbase;
+  if (G.layout == 0) st16<0>(p, v);
+  else if (G.layout == 1) st16<1>(p, v);
+  else st16<2>(p, v);
 }
 
 // Forward in-row stages of one operand.  Source: global row `g_src` (layout
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
     // pointwise product (Algorithm 4) in bit-reversed order
 #pragma unroll
     for (int u = 0; u < 16; u++) {
-      const uint64_t ahat = reduce4(sa[padj(G2.base + u)], K.q, K.two_q);
+      const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
       v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
     }
     rows_inv(v, P.c + off, single, sa, twi, logn, t, th, K.q, K.two_q, K.half_q1);
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q);
 #pragma unroll
       for (int u = 0; u < 16; u++) {
-        const uint64_t ahat = reduce4(sa[padj(G2.base + u)], K.q, K.two_q);
+        const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
         v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
       }
     }
