@@ -86,12 +86,32 @@ pm_status pm_find_params(uint32_t log2n, uint32_t nlimbs, uint32_t qbits,
  *             with the rule of pm_find_params
  *   device  : CUDA device ordinal the plan lives on
  * The plan builds, per limb, Psi_br[i] = psi^br(i) and
- * Psi^-1_br[i] = psi^-br(i) (times 1/2, see Sec. III-A halving) with their
- * Shoup companions floor(w 2^64 / q), and mu = floor(2^(2m+1)/q) of
- * Algorithm 4.  Device memory: 32 N + 64 bytes per limb.  Synchronous.
+ * Psi^-1_br[i] = psi^-br(i) with their Shoup companions floor(w 2^64 / q),
+ * mu = floor(2^(2m+1)/q) of Algorithm 4, and N^-1 for the inverse scaling.
+ * Device memory: 32 N + 128 bytes per limb.  Synchronous.
  * Errors: PM_ERR_N, PM_ERR_Q, PM_ERR_PSI, PM_ERR_OOM, PM_ERR_CUDA. */
 pm_status pm_plan_create(pm_plan **out, uint32_t log2n, uint32_t nlimbs,
                          const uint64_t *q, const uint64_t *psi, int device);
+
+/* Plan options (bit flags for pm_plan_create_ex). */
+enum {
+    /* Scale by 1/2 at every inverse butterfly output, as in the paper's Eq. 2
+     * (Zhang et al.'s halving, Sec. III-A); the inverse table then holds
+     * Psi^-1_br[i] / 2.  Without the flag the inverse butterflies are
+     * unscaled and 1/N is folded into the last inverse stage (its sum output
+     * times N^-1, its twiddle times N^-1).  Both give identical results; the
+     * default is faster on this GPU. */
+    PM_PLAN_HALVING = 1
+};
+
+/* pm_plan_create with options: `flags` is a combination of PM_PLAN_*;
+ * unknown bits give PM_ERR_ARG. */
+pm_status pm_plan_create_ex(pm_plan **out, uint32_t log2n, uint32_t nlimbs,
+                            const uint64_t *q, const uint64_t *psi, int device,
+                            uint32_t flags);
+
+/* The flags the plan was created with. */
+pm_status pm_plan_flags(const pm_plan *plan, uint32_t *flags);
 
 /* Release the plan and its device memory.  NULL is accepted. */
 pm_status pm_plan_destroy(pm_plan *plan);
@@ -110,9 +130,10 @@ pm_status pm_plan_info(const pm_plan *plan, uint32_t *log2n, uint32_t *nlimbs,
  * i.e. normal order in, bit-reversed order out (no->bo).  npoly >= 1. */
 pm_status pm_ntt_fwd(const pm_plan *plan, uint64_t *d_x, uint32_t npoly, void *stream);
 
-/* Inverse merged GS NTT (Algorithm 7 with the psi^-1 table and the 1/2
- * scaling at every butterfly, Sec. III-A), in place: the exact inverse of
- * pm_ntt_fwd (bit-reversed order in, normal order out, 1/N applied). */
+/* Inverse merged GS NTT (Algorithm 7 with the psi^-1 table, Eq. 1/Eq. 2),
+ * in place: the exact inverse of pm_ntt_fwd (bit-reversed order in, normal
+ * order out, 1/N applied -- folded into the last stage, or as 1/2 at every
+ * butterfly with PM_PLAN_HALVING). */
 pm_status pm_ntt_inv(const pm_plan *plan, uint64_t *d_x, uint32_t npoly, void *stream);
 
 /* Pointwise (Hadamard) product d_c = d_a . d_b mod q_l, reduced with

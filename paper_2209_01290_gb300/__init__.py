@@ -3,7 +3,8 @@
 c = a * b in Z_q[X]/(X^N + 1) computed as in arxiv 2209.01290, Eq. 2: merged
 Cooley-Tukey forward NTT (Algorithm 6), pointwise product with the Barrett
 variant of Algorithm 4, merged Gentleman-Sande inverse NTT (Algorithm 7) with
-the 1/N scaling folded in as halvings.  All arithmetic runs in the CUDA
+the 1/N scaling folded in (into the last inverse stage by default, or as a 1/2
+at every inverse butterfly with ``halving=True``).  All arithmetic runs in the CUDA
 library built from ``csrc/`` (C ABI in ``include/pm.h``); this package only
 marshals torch tensors (device memory, streams) into that ABI.
 
@@ -41,11 +42,14 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A device-resident plan for one (N, {q_l}, {psi_l})."""
 
-    def __init__(self, n: int, qs, psis=None, device: int = 0):
+    def __init__(self, n: int, qs, psis=None, device: int = 0, halving: bool = False):
+        """halving=True scales by 1/2 at every inverse butterfly (the paper's
+        Eq. 2 form); the default folds 1/N into the last inverse stage."""
         self.n = n
         self.log2n = _log2(n)
         self.device = device
-        self._h = capi.pm_plan_create(self.log2n, list(qs), psis, device)
+        self._h = capi.pm_plan_create_ex(self.log2n, list(qs), psis, device,
+                                         capi.PM_PLAN_HALVING if halving else 0)
         _, self.nlimbs, self.qs, self.psis = capi.pm_plan_info(self._h)
 
     # -- lifetime

@@ -27,6 +27,8 @@ _pu64, _pu32 = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)
 SIGNATURES = {
     "pm_find_params": (_i32, [_u32, _u32, _u32, _pu64, _pu64]),
     "pm_plan_create": (_i32, [ctypes.POINTER(_vp), _u32, _u32, _pu64, _pu64, _i32]),
+    "pm_plan_create_ex": (_i32, [ctypes.POINTER(_vp), _u32, _u32, _pu64, _pu64, _i32, _u32]),
+    "pm_plan_flags": (_i32, [_vp, _pu32]),
     "pm_plan_destroy": (_i32, [_vp]),
     "pm_plan_reserve": (_i32, [_vp, _u32, _vp]),
     "pm_plan_info": (_i32, [_vp, _pu32, _pu32, _pu64, _pu64]),
@@ -97,13 +99,26 @@ def pm_find_params(log2n: int, nlimbs: int, qbits: int = 60):
     return list(q), list(psi)
 
 
+PM_PLAN_HALVING = 1
+
+
 def pm_plan_create(log2n: int, qs, psis=None, device: int = 0) -> int:
+    return pm_plan_create_ex(log2n, qs, psis, device, 0)
+
+
+def pm_plan_create_ex(log2n: int, qs, psis=None, device: int = 0, flags: int = 0) -> int:
     L = len(qs)
     q = (ctypes.c_uint64 * L)(*[int(x) for x in qs])
     p = (ctypes.c_uint64 * L)(*[int(x) for x in psis]) if psis is not None else None
     out = ctypes.c_void_p()
-    _call("pm_plan_create", ctypes.byref(out), log2n, L, q, p, device)
+    _call("pm_plan_create_ex", ctypes.byref(out), log2n, L, q, p, device, flags)
     return out.value
+
+
+def pm_plan_flags(plan: int) -> int:
+    f = ctypes.c_uint32()
+    _call("pm_plan_flags", plan, ctypes.byref(f))
+    return f.value
 
 
 def pm_plan_destroy(plan: int) -> None:

@@ -28,7 +28,12 @@ __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint6
   return w * y + qh * (0 - q);
 }
 
-__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
+// x - m if x >= m else x, for x < 2^63 + m and m <= 2^63 (all lazy values here
+// are < 2^62): the sign of x - m decides, one compare on the high word.
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) {
+  const uint64_t t = x - m;
+  return (int64_t)t < 0 ? x : t;
+}
 
 // Merged-CT butterfly (Algorithm 6 body):
 //   (x, y) <- (x + w y, x - w y) mod q
@@ -58,6 +63,36 @@ __device__ __forceinline__ void gs_bfly_half(uint64_t& x, uint64_t& y, uint64_t 
   const uint64_t d = x - y + two_q;                // (0, 4q)
   x = half_lazy(s, half_q1);                       // [0, 2q)
   y = mul_shoup_lazy(d, w2, w2p, q);               // [0, 2q)
+}
+
+// Merged-GS butterfly (Algorithm 7 body) without scaling:
+//   (x, y) <- (x + y, w (x - y)) mod q
+// on lazy representatives in [0, 2q); 1/N is applied by gs_bfly_last.
+__device__ __forceinline__ void gs_bfly(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
+                                        uint64_t q, uint64_t two_q) {
+  const uint64_t s = csub(x + y, two_q);           // [0, 2q)
+  const uint64_t d = x - y + two_q;                // (0, 4q)
+  x = s;
+  y = mul_shoup_lazy(d, w, wp, q);                 // [0, 2q)
+}
+
+// The last GS stage (k = N/2, twiddle Psi^-1_br[1]) with 1/N folded in:
+//   (x, y) <- ((x + y) / N, w (x - y) / N) mod q, results in [0, 2q).
+__device__ __forceinline__ void gs_bfly_last(uint64_t& x, uint64_t& y, const LimbConst& k) {
+  const uint64_t s = x + y;                        // [0, 4q)
+  const uint64_t d = x - y + k.two_q;              // (0, 4q)
+  x = mul_shoup_lazy(s, k.ninv, k.ninv_p, k.q);
+  y = mul_shoup_lazy(d, k.w1ninv, k.w1ninv_p, k.q);
+}
+
+// One GS butterfly in the plan's scaling mode.
+template <bool HALVE>
+__device__ __forceinline__ void gs_bfly_mode(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
+                                             uint64_t q, uint64_t two_q, uint64_t hq) {
+  if constexpr (HALVE)
+    gs_bfly_half(x, y, w, wp, q, two_q, hq);
+  else
+    gs_bfly(x, y, w, wp, q, two_q);
 }
 
 // [0, 4q) -> [0, q)

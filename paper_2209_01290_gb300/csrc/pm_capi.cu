@@ -74,6 +74,7 @@ struct pm_plan {
   int device = 0;
   int num_sms = 0;
   uint32_t logn = 0, nlimbs = 0;
+  uint32_t flags = 0;
   std::vector<uint64_t> q, psi;
   pm::LimbConst* d_lc = nullptr;
   pm::TwPair* d_twf = nullptr;
@@ -112,6 +113,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.logn = p->logn;
   P.nlimbs = p->nlimbs;
   P.nunits = npoly * p->nlimbs;
+  P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
   return P;
 }
 
@@ -223,7 +225,13 @@ pm_status pm_find_params(uint32_t log2n, uint32_t nlimbs, uint32_t qbits, uint64
 
 pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const uint64_t* q,
                          const uint64_t* psi, int device) {
+  return pm_plan_create_ex(out, log2n, nlimbs, q, psi, device, 0);
+}
+
+pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const uint64_t* q,
+                            const uint64_t* psi, int device, uint32_t flags) {
   if (!out) return fail(PM_ERR_ARG, "out is NULL");
+  if (flags & ~(uint32_t)PM_PLAN_HALVING) return fail(PM_ERR_ARG, "unknown plan flags 0x%x", flags);
   *out = nullptr;
   if (log2n < 1 || log2n > kMaxLog2N) return fail(PM_ERR_N, "log2n=%u outside [1,17]", log2n);
   if (nlimbs < 1 || nlimbs > kMaxLimbs) return fail(PM_ERR_ARG, "nlimbs=%u outside [1,1024]", nlimbs);
@@ -259,6 +267,7 @@ pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const u
   pm_plan* p = new (std::nothrow) pm_plan();
   if (!p) return fail(PM_ERR_OOM, "host allocation failed");
   p->device = device;
+  p->flags = flags;
   p->logn = log2n;
   p->nlimbs = nlimbs;
   p->q.assign(q, q + nlimbs);
@@ -276,7 +285,8 @@ pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const u
   std::vector<pm::LimbConst> lc(nlimbs);
   std::vector<pm::TwPair> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
   for (uint32_t l = 0; l < nlimbs; ++l)
-    pm::host::build_limb(log2n, q[l], psis[l], &lc[l], &twf[(size_t)l * n], &twi[(size_t)l * n]);
+    pm::host::build_limb(log2n, q[l], psis[l], (flags & PM_PLAN_HALVING) != 0, &lc[l],
+                         &twf[(size_t)l * n], &twi[(size_t)l * n]);
   const size_t tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair);
   if ((e = cudaMalloc(&p->d_lc, nlimbs * sizeof(pm::LimbConst))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_twf, tw_bytes)) != cudaSuccess ||
@@ -298,6 +308,14 @@ pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const u
 
 pm_status pm_plan_destroy(pm_plan* plan) {
   destroy_plan(plan);
+  return ok();
+}
+
+pm_status pm_plan_flags(const pm_plan* plan, uint32_t* flags) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!flags) return fail(PM_ERR_ARG, "flags is NULL");
+  *flags = plan->flags;
   return ok();
 }
 

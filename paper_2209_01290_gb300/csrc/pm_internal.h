@@ -21,7 +21,7 @@ struct KParams {
   uint32_t logn;
   uint32_t nlimbs;
   uint32_t nunits;       // npoly * nlimbs
-  uint32_t pad;
+  uint32_t halving;      // 1: per-stage 1/2 scaling (table holds w/2); 0: 1/N folded at the end
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the

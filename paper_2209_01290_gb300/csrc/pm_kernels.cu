@@ -76,7 +76,7 @@ __device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict
 // 16 words.  GS stages sig0..sig0+3 (k = 2^sig); the group is block g of
 // 2^(sig0+4) words.  Stage sig0+st pairs (u, u + 2^st) with twiddle
 // Psi^-1_br[(N >> (sig0+st+1)) + g 2^(3-st) + (u >> (st+1))] (times 1/2).
-template <int ST>
+template <int ST, bool HALVE>
 __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                            uint32_t logn, uint32_t sig0, uint32_t g,
                                            uint64_t q, uint64_t two_q, uint64_t hq) {
@@ -87,17 +87,18 @@ __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __re
     const TwPair t = ld_tw(tw + base + blk);
 #pragma unroll
     for (int u0 = 0; u0 < h; u0++)
-      gs_bfly_half(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
+      gs_bfly_mode<HALVE>(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
   }
 }
 
+template <bool HALVE>
 __device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                      uint32_t logn, uint32_t sig0, uint32_t g,
                                      uint64_t q, uint64_t two_q, uint64_t hq) {
-  gs16_stage<0>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<1>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<2>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<3>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<0, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<1, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<2, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
+  gs16_stage<3, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
 }
 
 // Merged CT on a column of R words (the first log2 R stages of the N-point
@@ -126,33 +127,41 @@ __device__ __forceinline__ void ct_col(uint64_t (&x)[R], const TwPair* __restric
 
 // Merged GS on a column of R words (the last log2 R stages): the GS stage
 // with k = 4096 * 2^E pairs (t, t + 2^E) with twiddle
-// Psi^-1_br[(R >> (E+1)) + (t >> (E+1))] (times 1/2).
-template <int R, int E>
+// Psi^-1_br[(R >> (E+1)) + (t >> (E+1))].  Without per-stage halving the
+// final stage (2^E = R/2, the transform's last) folds in 1/N.
+template <int R, int E, bool HALVE>
 __device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                             uint64_t q, uint64_t two_q, uint64_t hq) {
+                                             const LimbConst& K) {
   if constexpr ((1 << E) < R) {
     constexpr int h = 1 << E;
+    if constexpr (!HALVE && 2 * h == R) {
 #pragma unroll
-    for (int blk = 0; blk < R / (2 * h); blk++) {
-      const TwPair t = ld_tw(tw + (R >> (E + 1)) + blk);
+      for (int u0 = 0; u0 < h; u0++) gs_bfly_last(x[u0], x[u0 + h], K);
+    } else {
 #pragma unroll
-      for (int u0 = 0; u0 < h; u0++)
-        gs_bfly_half(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
+      for (int blk = 0; blk < R / (2 * h); blk++) {
+        const TwPair t = ld_tw(tw + (R >> (E + 1)) + blk);
+#pragma unroll
+        for (int u0 = 0; u0 < h; u0++)
+          gs_bfly_mode<HALVE>(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, K.q,
+                              K.two_q, K.half_q1);
+      }
     }
-    gs_col_stage<R, E + 1>(x, tw, q, two_q, hq);
+    gs_col_stage<R, E + 1, HALVE>(x, tw, K);
   }
 }
 
-template <int R>
+template <int R, bool HALVE>
 __device__ __forceinline__ void gs_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                       uint64_t q, uint64_t two_q, uint64_t hq) {
-  gs_col_stage<R, 0>(x, tw, q, two_q, hq);
+                                       const LimbConst& K) {
+  gs_col_stage<R, 0, HALVE>(x, tw, K);
 }
 
 __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
   LimbConst k;
   const ulonglong2* s = reinterpret_cast<const ulonglong2*>(p);
-  ulonglong2 v0 = __ldg(s), v1 = __ldg(s + 1), v2 = __ldg(s + 2);
+  const ulonglong2 v0 = __ldg(s), v1 = __ldg(s + 1), v2 = __ldg(s + 2), v3 = __ldg(s + 3),
+                   v4 = __ldg(s + 4);
   k.q = v0.x;
   k.two_q = v0.y;
   k.half_q1 = v1.x;
@@ -160,7 +169,11 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
   k.m = (uint32_t)v2.x;
   k.sh1 = (uint32_t)(v2.x >> 32);
   k.sh2 = (uint32_t)v2.y;
-  k.pad0 = 0;
+  k.halving = (uint32_t)(v2.y >> 32);
+  k.ninv = v3.x;
+  k.ninv_p = v3.y;
+  k.w1ninv = v4.x;
+  k.w1ninv_p = v4.y;
   return k;
 }
 
@@ -258,21 +271,28 @@ __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_sr
 // Inverse in-row stages (1/2-scaled).  v holds layout-2 words on entry.
 // The last pass writes layout 0 either to the global row `g_dst`
 // (canonical if `final`) or, if null, back to smem.
+// With `final` (the row is the whole transform, N = 4096) and no per-stage
+// halving, the outputs are multiplied by N^-1 before the store.
+template <bool HALVE>
 __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, bool final,
                                          uint64_t* s, const TwPair* __restrict__ twi,
-                                         uint32_t logn, uint32_t t, int th, uint64_t q,
-                                         uint64_t two_q, uint64_t hq) {
+                                         uint32_t logn, uint32_t t, int th, const LimbConst& K) {
+  const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
     const PassGeo G = pass_geo(2 - p, th, t);
     if (p > 0) ld_smem16(v, s, G);
-    gs16(v, twi, logn, 4 * p, G.g, q, two_q, hq);
+    gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq);
     if (p < 2) {
       st_smem16(s, G, v);
       __syncthreads();
     }
   }
   if (g_dst) {
+    if (!HALVE && final) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) v[u] = mul_shoup_lazy(v[u], K.ninv, K.ninv_p, q);
+    }
 #pragma unroll
     for (int u = 0; u < 16; u++) __stcs(g_dst + th + 256 * u, final ? csub(v[u], q) : v[u]);
   } else {
@@ -286,7 +306,7 @@ __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, boo
 // the row is the whole unit (polymul reads a, b; output canonical).  For
 // n > 12, polymul reads the column-transformed operands from c and the
 // scratch s and leaves lazy c' rows for k_col_inv.
-template <int MODE>
+template <int MODE, bool HALVE>
 __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
   extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t logn = P.logn;
@@ -311,7 +331,7 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
       v[u] = w.x;
       v[u + 1] = w.y;
     }
-    rows_inv(v, P.c + off, single, sa, twi, logn, t, th, K.q, K.two_q, K.half_q1);
+    rows_inv<HALVE>(v, P.c + off, single, sa, twi, logn, t, th, K);
   } else if constexpr (MODE == MODE_FWD) {
     rows_fwd(v, P.c + off, sa, twf, logn, t, th, K.q, K.two_q);
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + off + 16 * th);
@@ -333,7 +353,7 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
       const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
       v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
     }
-    rows_inv(v, P.c + off, single, sa, twi, logn, t, th, K.q, K.two_q, K.half_q1);
+    rows_inv<HALVE>(v, P.c + off, single, sa, twi, logn, t, th, K);
   }
 }
 
@@ -366,7 +386,7 @@ __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
 
 // Inverse column stages (the last log2 R stages of Algorithm 7, 1/2-scaled)
 // plus the reduction to [0, q); in place on c.
-template <int R>
+template <int R, bool HALVE>
 __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
   const uint32_t logn = P.logn;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -380,14 +400,14 @@ __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
   uint64_t x[R];
 #pragma unroll
   for (int t = 0; t < R; t++) x[t] = p[(size_t)t * kRow];
-  gs_col<R>(x, twi, K.q, K.two_q, K.half_q1);
+  gs_col<R, HALVE>(x, twi, K);
 #pragma unroll
   for (int t = 0; t < R; t++) __stcs(p + (size_t)t * kRow, csub(x[t], K.q));
 }
 
 // N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
 // (k = 4096) runs between global memory and smem; rows as in k_rows.
-template <int MODE>
+template <int MODE, bool HALVE>
 __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
   extern __shared__ __align__(16) uint64_t smem[];
   constexpr uint32_t logn = 13;
@@ -450,23 +470,27 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       v[u + 1] = w.y;
     }
   }
-  rows_inv(v, nullptr, false, sa, twi, logn, rho, th, K.q, K.two_q, K.half_q1);
+  rows_inv<HALVE>(v, nullptr, false, sa, twi, logn, rho, th, K);
   __syncthreads();
-  // last GS stage (k = 4096), twiddle Psi^-1_br[1] (times 1/2), then reduce
+  // last GS stage (k = 4096, twiddle Psi^-1_br[1]; 1/N folded in unless the
+  // plan halves at every stage), then reduce
   const TwPair w = ld_tw(twi + 1);
   uint64_t* dst = P.c + base;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     const int c = tid + 512 * k;
     uint64_t x0 = sA[padj(c)], x1 = sA[kRowPad + padj(c)];
-    gs_bfly_half(x0, x1, w.w, w.wp, K.q, K.two_q, K.half_q1);
+    if constexpr (HALVE)
+      gs_bfly_half(x0, x1, w.w, w.wp, K.q, K.two_q, K.half_q1);
+    else
+      gs_bfly_last(x0, x1, K);
     __stcs(dst + c, csub(x0, K.q));
     __stcs(dst + kRow + c, csub(x1, K.q));
   }
 }
 
 // N <= 2^11: one CTA per unit, Algorithms 6 and 7 stage by stage in smem.
-template <int MODE>
+template <int MODE, bool HALVE>
 __global__ void __launch_bounds__(256) k_small(KParams P) {
   extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t logn = P.logn, n = 1u << logn;
@@ -509,8 +533,12 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
   for (uint32_t m = n >> 1, k = 1; m >= 1; m >>= 1, k <<= 1) {
     for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
       const uint32_t i = b / k, j = 2 * i * k + (b % k);
-      const TwPair w = ld_tw(twi + m + i);
-      gs_bfly_half(xa[j], xa[j + k], w.w, w.wp, q, two_q, K.half_q1);
+      if (!HALVE && m == 1) {
+        gs_bfly_last(xa[j], xa[j + k], K);  // last stage: 1/N folded in
+      } else {
+        const TwPair w = ld_tw(twi + m + i);
+        gs_bfly_mode<HALVE>(xa[j], xa[j + k], w.w, w.wp, q, two_q, K.half_q1);
+      }
     }
     __syncthreads();
   }
@@ -566,7 +594,10 @@ template <int R>
 static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
   const size_t threads = (size_t)P.nunits * kRow;
   const unsigned blocks = (unsigned)((threads + 255) / 256);
-  k_col_inv<R><<<blocks, 256, 0, st>>>(P);
+  if (P.halving)
+    k_col_inv<R, true><<<blocks, 256, 0, st>>>(P);
+  else
+    k_col_inv<R, false><<<blocks, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -597,37 +628,50 @@ constexpr int kFused13Smem = 4 * kRowPad * 8;
 
 template <int MODE>
 static cudaError_t rows(const KParams& P, cudaStream_t st) {
-  const int smem = kRowsSmem;
   const unsigned blocks = P.nunits << (P.logn - kRowLog);
-  k_rows<MODE><<<blocks, 256, smem, st>>>(P);
+  if (P.halving)
+    k_rows<MODE, true><<<blocks, 256, kRowsSmem, st>>>(P);
+  else
+    k_rows<MODE, false><<<blocks, 256, kRowsSmem, st>>>(P);
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t fused13(const KParams& P, cudaStream_t st) {
-  const int smem = kFused13Smem;
-  k_fused13<MODE><<<P.nunits, 512, smem, st>>>(P);
+  if (P.halving)
+    k_fused13<MODE, true><<<P.nunits, 512, kFused13Smem, st>>>(P);
+  else
+    k_fused13<MODE, false><<<P.nunits, 512, kFused13Smem, st>>>(P);
   return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t small(const KParams& P, cudaStream_t st) {
   const int smem = 2 * (1 << P.logn) * 8;
-  k_small<MODE><<<P.nunits, 256, smem, st>>>(P);
+  if (P.halving)
+    k_small<MODE, true><<<P.nunits, 256, smem, st>>>(P);
+  else
+    k_small<MODE, false><<<P.nunits, 256, smem, st>>>(P);
   return cudaGetLastError();
+}
+
+template <bool H>
+static cudaError_t prepare_mode() {
+  cudaError_t e;
+  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL, H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows<MODE_FWD, H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows<MODE_INV, H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL, H>, kFused13Smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_FWD, H>, kFused13Smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_INV, H>, kFused13Smem)) != cudaSuccess) return e;
+  return cudaSuccess;
 }
 
 // Opt the large-smem kernels in to their dynamic shared memory on the current
 // device (once per device, before the first launch).
 cudaError_t kernels_prepare() {
-  cudaError_t e;
-  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows<MODE_FWD>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows<MODE_INV>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL>, kFused13Smem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_FWD>, kFused13Smem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_INV>, kFused13Smem)) != cudaSuccess) return e;
-  return cudaSuccess;
+  cudaError_t e = prepare_mode<false>();
+  return e != cudaSuccess ? e : prepare_mode<true>();
 }
 
 static inline cudaError_t mark(const PhaseEvents* pe, int k, cudaStream_t st) {

@@ -4,9 +4,10 @@
 //  * NTT-friendly primes: q prime with 2N | q - 1, below a bit bound.
 //  * psi: a primitive 2N-th root of unity mod q, chosen by the fixed rule
 //    "first x = 2, 3, ... whose power x^((q-1)/2N) has psi^N = -1".
-//  * Per-limb tables: Psi_br[i] = psi^br(i) and (psi^-1)^br(i) * 2^-1 for the
-//    halving GS butterflies, each with its Shoup companion floor(w 2^64 / q),
-//    and Algorithm 4's mu = floor(2^(2m+1) / q).
+//  * Per-limb tables: Psi_br[i] = psi^br(i) and (psi^-1)^br(i) (times 2^-1
+//    when the plan uses per-stage halving), each with its Shoup companion
+//    floor(w 2^64 / q); Algorithm 4's mu = floor(2^(2m+1) / q); N^-1 and
+//    Psi^-1_br[1] * N^-1 for folding 1/N into the last inverse stage.
 #include <cstdint>
 #include <vector>
 
@@ -111,8 +112,8 @@ static inline uint32_t reverse_bits(uint32_t x, uint32_t nbits) {
   return r;
 }
 
-void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, LimbConst* lc, TwPair* twf,
-                TwPair* twi) {
+void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbConst* lc,
+                TwPair* twf, TwPair* twi) {
   const uint32_t n = 1u << log2n;
   const uint32_t m = bit_length(q);
   lc->q = q;
@@ -122,8 +123,7 @@ void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, LimbConst* lc, TwPair*
   lc->m = m;
   lc->sh1 = m - 2;
   lc->sh2 = m + 3;
-  lc->pad0 = 0;
-  lc->pad1[0] = lc->pad1[1] = lc->pad1[2] = 0;
+  lc->halving = halving ? 1 : 0;
   // powers psi^e and psi^-e for e < N
   const uint64_t psi_inv = pow_mod(psi, 2 * (uint64_t)n - 1, q);  // psi^(2N) = 1
   const uint64_t inv2 = (q + 1) / 2;
@@ -137,12 +137,19 @@ void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, LimbConst* lc, TwPair*
   for (uint32_t i = 0; i < n; ++i) {
     const uint32_t r = reverse_bits(i, log2n);
     const uint64_t wf = fw[r];
-    const uint64_t wi = mul_mod(iv[r], inv2, q);
+    const uint64_t wi = halving ? mul_mod(iv[r], inv2, q) : iv[r];
     twf[i].w = wf;
     twf[i].wp = shoup_companion(wf, q);
     twi[i].w = wi;
     twi[i].wp = shoup_companion(wi, q);
   }
+  // N^-1 = (2^-1)^log2n; Psi^-1_br[1] = psi^-(N/2) (br(1) = N/2)
+  const uint64_t ninv = pow_mod(inv2, log2n, q);
+  const uint64_t w1 = n > 1 ? iv[reverse_bits(1, log2n)] : 1;
+  lc->ninv = ninv;
+  lc->ninv_p = shoup_companion(ninv, q);
+  lc->w1ninv = mul_mod(w1, ninv, q);
+  lc->w1ninv_p = shoup_companion(lc->w1ninv, q);
 }
 
 }  // namespace host

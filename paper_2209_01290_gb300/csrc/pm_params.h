@@ -16,8 +16,10 @@ int largest_ntt_primes(uint32_t log2n, uint32_t qbits, uint32_t count, uint64_t*
 // psi for q by the fixed search rule; 0 if q is not = 1 mod 2N or none found.
 uint64_t default_psi(uint64_t q, uint32_t log2n);
 // Limb constants and twiddle tables (host arrays of N entries).
-void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, LimbConst* lc, TwPair* twf,
-                TwPair* twi);
+// halving: the inverse table holds Psi^-1_br[i] / 2 (per-stage halving of
+// Sec. III-A); otherwise Psi^-1_br[i] and 1/N is folded into the last stage.
+void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbConst* lc,
+                TwPair* twf, TwPair* twi);
 
 }  // namespace host
 }  // namespace pm

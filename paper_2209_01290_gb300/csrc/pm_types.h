@@ -13,8 +13,11 @@ struct alignas(64) LimbConst {
   uint32_t m;        // len(q), bit length
   uint32_t sh1;      // m - 2   (Algorithm 4, step 1 shift)
   uint32_t sh2;      // m + 3   (Algorithm 4, step 2 shift)
-  uint32_t pad0;
-  uint64_t pad1[3];
+  uint32_t halving;  // 1: the inverse table holds w/2 and every GS butterfly halves
+  uint64_t ninv;     // N^-1 mod q            (1/N folded into the last GS stage)
+  uint64_t ninv_p;   //   its Shoup companion
+  uint64_t w1ninv;   // Psi^-1_br[1] * N^-1 mod q
+  uint64_t w1ninv_p; //   its Shoup companion
 };
 
 // Twiddle factor with its Shoup companion floor(w * 2^64 / q), 16 bytes.

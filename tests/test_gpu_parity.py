@@ -20,19 +20,21 @@ def torch_cuda():
     return torch
 
 
-def _plan(log2n, nlimbs, qbits=60):
+def _plan(log2n, nlimbs, qbits=60, halving=False):
     from paper_2209_01290_gb300 import Plan, capi
     qs, psis = capi.pm_find_params(log2n, nlimbs, qbits)
-    return Plan(1 << log2n, qs, psis), qs, psis
+    return Plan(1 << log2n, qs, psis, halving=halving), qs, psis
 
 
+@pytest.mark.parametrize("halving", [False, True], ids=["fold1N", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
-def test_polymul_all_sizes(torch_cuda, oracle, log2n):
+def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving):
     """Every code path: radix-2 smem kernel (N <= 2^11), single-row kernel
-    (2^12), one-CTA 2^13 kernel, column split (2^14..2^17); 2 polys x 3 limbs."""
+    (2^12), one-CTA 2^13 kernel, column split (2^14..2^17); 2 polys x 3 limbs;
+    1/N folded into the last stage or applied as per-stage halving."""
     n = 1 << log2n
     L, P = (3, 2) if log2n <= 15 else (2, 1)
-    plan, qs, psis = _plan(log2n, L)
+    plan, qs, psis = _plan(log2n, L, halving=halving)
     a, b = operands(1000 + log2n, qs, P, n)
     want = oracle_polymul_batch(oracle, a, b, qs, psis)
     got = to_host(plan.polymul(to_dev(a), to_dev(b)))
@@ -40,13 +42,14 @@ def test_polymul_all_sizes(torch_cuda, oracle, log2n):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("halving", [False, True], ids=["fold1N", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
-def test_ntt_fwd_inv_all_sizes(torch_cuda, oracle, log2n):
+def test_ntt_fwd_inv_all_sizes(torch_cuda, oracle, log2n, halving):
     """Forward NTT equals the oracle's bo-order transform; inverse equals the
     oracle's inverse; inverse(forward(x)) = x."""
     n = 1 << log2n
     L = 2
-    plan, qs, psis = _plan(log2n, L)
+    plan, qs, psis = _plan(log2n, L, halving=halving)
     x, y = operands(2000 + log2n, qs, 1, n)
     d = to_dev(x)
     plan.ntt_fwd_(d)
