@@ -148,6 +148,24 @@ pm_status pm_pointwise(const pm_plan *plan, const uint64_t *d_a, const uint64_t 
 pm_status pm_polymul(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
                      uint64_t *d_c, uint32_t npoly, void *stream);
 
+/* Same product as pm_polymul, for callers that must not allocate device
+ * memory: code running while another memory manager owns the device pool,
+ * or latency-critical paths that cannot take the device-wide synchronisation
+ * of cudaFree.  The paper has no counterpart; this is a deployment variant.
+ * The caller still provides a, b and c.  For N >= 2^14 the products need
+ * scratch: it is a fixed 16 MiB array inside the library (2^21 words, held
+ * on every device that loads the library until the process exits), so the
+ * batch must satisfy npoly * nlimbs * N <= 2^21; larger batches are
+ * rejected with PM_ERR_ARG.  No cudaMalloc/cudaFree or other allocating
+ * call is made.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) once; make that first call before any
+ * stream capture.  All calls share the one array and the scratch needs no
+ * clearing (every word is written before it is read within a call), so calls
+ * that overlap on the GPU -- on different streams or from several threads --
+ * race on it: issue them on one stream.  N < 2^14 uses no scratch. */
+pm_status pm_polymul_noalloc(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
+                             uint64_t *d_c, uint32_t npoly, void *stream);
+
 /* Same product from and to HOST memory: copies h_a, h_b to the device
  * buffers d_a, d_b, runs pm_polymul into d_c and copies d_c back to h_c, all
  * on `stream`, in chunks so that copies and compute of successive chunks

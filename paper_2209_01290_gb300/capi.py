@@ -37,6 +37,7 @@ SIGNATURES = {
     "pm_pointwise": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_polymul": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_polymul_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_polymul_noalloc": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_check_reduced": (_i32, [_vp, _vp, _u32, _vp]),
     "pm_plan_sync": (_i32, [_vp, _vp]),
     "pm_plan_set_phase_events": (_i32, [_vp, ctypes.POINTER(_vp), _i32]),
@@ -153,6 +154,12 @@ def pm_pointwise(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: in
 
 def pm_polymul(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: int = 0) -> None:
     _call("pm_polymul", plan, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_polymul_noalloc(plan: int, d_a: int, d_b: int, d_c: int, npoly: int,
+                       stream: int = 0) -> None:
+    """Allocation-free product (fixed 16 MiB library scratch, see pm.h)."""
+    _call("pm_polymul_noalloc", plan, d_a, d_b, d_c, npoly, stream)
 
 
 def pm_polymul_host(plan: int, h_a: int, h_b: int, h_c: int, d_a: int, d_b: int, d_c: int,

@@ -408,6 +408,74 @@ pm_status pm_polymul(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d
   return s == PM_OK ? ok() : s;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Allocation-free polymul.  Callers that must not allocate device memory
+// (for example code running while another component owns the device
+// memory pool, or latency-critical code that cannot accept the device-wide
+// synchronisation of cudaFree) use this entry point instead of pm_polymul:
+// the column-split path's scratch lives in the fixed array below, which is
+// part of the library image and exists on every device that loads it.
+constexpr uint64_t kNoAllocScratchWords = (uint64_t)1 << 21;  // 16 MiB
+
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+std::vector<std::pair<int, uint64_t*>> g_noalloc_ptr;  // device -> device address
+
+// Device address of g_noalloc_scratch on the current device `dev`, looked up
+// once per device.  In host code the array's name is only a host-side
+// stand-in, so the kernels must be given this looked-up address.
+pm_status noalloc_scratch(int dev, uint64_t** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  for (auto& e : g_noalloc_ptr)
+    if (e.first == dev) {
+      *out = e.second;
+      return PM_OK;
+    }
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+  g_noalloc_ptr.emplace_back(dev, (uint64_t*)ptr);
+  *out = (uint64_t*)ptr;
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_polymul_noalloc(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
+                             uint64_t* d_c, uint32_t npoly, void* stream) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  pm::KParams P = base_params(plan, npoly);
+  P.a = d_a;
+  P.b = d_b;
+  P.c = d_c;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (pm::polymul_needs_scratch(plan->logn)) {
+    const uint64_t words = (uint64_t)P.nunits << plan->logn;
+    if (words > kNoAllocScratchWords)
+      return fail(PM_ERR_ARG,
+                  "pm_polymul_noalloc: batch needs %llu scratch words, the static area holds "
+                  "%llu (npoly * nlimbs * N <= 2^21)",
+                  (unsigned long long)words, (unsigned long long)kNoAllocScratchWords);
+    s = noalloc_scratch(plan->device, &P.s);
+    if (s != PM_OK) return s;
+  }
+  cudaError_t e = pm::launch_polymul(P, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "polymul launch");
+  return ok();
+}
+
 pm_status pm_polymul_host(const pm_plan* plan, const uint64_t* h_a, const uint64_t* h_b,
                           uint64_t* h_c, uint64_t* d_a, uint64_t* d_b, uint64_t* d_c,
                           uint32_t npoly, void* stream) {
