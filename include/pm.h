@@ -181,6 +181,40 @@ pm_status pm_polymul_host(const pm_plan *plan, const uint64_t *h_a, const uint64
 pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t npoly,
                            void *stream);
 
+/* How pm_polymul is launched for N >= 2^13 (a performance choice only; the
+ * results are identical):
+ *   PM_VARIANT_SPLIT      : three launches -- forward column stages, in-row
+ *                           stages with the pointwise product, inverse column
+ *                           stages (N = 2^13: one launch);
+ *   PM_VARIANT_PERSISTENT : one persistent launch whose CTAs take column and
+ *                           row tasks of all units from a work queue in a
+ *                           software-pipelined order (lag_fwd / lag_inv are
+ *                           the pipeline distances in units, ctas_per_sm the
+ *                           resident CTAs per SM).  Uses a control block of
+ *                           16 + 8 * units bytes in the stream's scratch.
+ * The default is PERSISTENT with 3 CTAs per SM, lags 8 and 16. */
+enum { PM_VARIANT_SPLIT = 0, PM_VARIANT_PERSISTENT = 1 };
+typedef struct pm_tuning {
+    int32_t variant;
+    uint32_t ctas_per_sm;
+    uint32_t lag_fwd;
+    uint32_t lag_inv;
+} pm_tuning;
+
+/* Set / read the plan's launch choice.  PM_ERR_ARG for out-of-range values. */
+pm_status pm_plan_tune(pm_plan *plan, const pm_tuning *t);
+pm_status pm_plan_get_tuning(const pm_plan *plan, pm_tuning *t);
+
+/* Test hook: fault injection on the host side of the next persistent
+ * polymul launch on this plan (kind 0 clears it).
+ *   PM_FAULT_WITHHOLD_SIGNAL : the launch's row tasks wait for one more
+ *     "column stage done" signal than will ever arrive, so their bounded
+ *     waits run out (about a second); pm_plan_sync then reports
+ *     PM_ERR_TIMEOUT and the results of that call are invalid.  Nothing
+ *     faults on the device and later calls work normally. */
+enum { PM_FAULT_WITHHOLD_SIGNAL = 1 };
+pm_status pm_plan_inject_fault(pm_plan *plan, int kind);
+
 /* Profiling hook for pm_polymul: with n > 0, each later pm_polymul on this
  * plan records events[k] (cudaEvent_t, created by the caller) on its stream
  * after phase k: k = 0 before the first kernel, then after each kernel
@@ -189,7 +223,9 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
 pm_status pm_plan_set_phase_events(pm_plan *plan, void *const *events, int n);
 
 /* Wait for all work the plan's calls queued on `stream` and report any
- * device-side error. */
+ * device-side error, including PM_ERR_TIMEOUT when a persistent launch on
+ * that stream gave up waiting for a dependency (its results are then not
+ * valid).  Each device-side wait is bounded (about a second). */
 pm_status pm_plan_sync(const pm_plan *plan, void *stream);
 
 /* Message for the last failing call on this host thread ("" if none). */

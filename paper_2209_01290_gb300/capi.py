@@ -40,6 +40,9 @@ SIGNATURES = {
     "pm_polymul_noalloc": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_check_reduced": (_i32, [_vp, _vp, _u32, _vp]),
     "pm_plan_sync": (_i32, [_vp, _vp]),
+    "pm_plan_tune": (_i32, [_vp, ctypes.c_void_p]),
+    "pm_plan_inject_fault": (_i32, [_vp, _i32]),
+    "pm_plan_get_tuning": (_i32, [_vp, ctypes.c_void_p]),
     "pm_plan_set_phase_events": (_i32, [_vp, ctypes.POINTER(_vp), _i32]),
     "pm_last_error": (ctypes.c_char_p, []),
     "pm_last_error_string": (_i32, [ctypes.c_char_p, _sz]),
@@ -179,6 +182,39 @@ def pm_plan_set_phase_events(plan: int, events) -> None:
     """events: list of cudaEvent_t handles (ints), at most 4; [] turns it off."""
     arr = (ctypes.c_void_p * max(1, len(events)))(*[int(e) for e in events])
     _call("pm_plan_set_phase_events", plan, arr, len(events))
+
+
+PM_VARIANT_SPLIT = 0
+PM_VARIANT_PERSISTENT = 1
+
+
+class PmTuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_uint32),
+                ("lag_fwd", ctypes.c_uint32), ("lag_inv", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"variant": "persistent" if self.variant == PM_VARIANT_PERSISTENT else "split",
+                "ctas_per_sm": self.ctas_per_sm, "lag_fwd": self.lag_fwd,
+                "lag_inv": self.lag_inv}
+
+
+def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 3, lag_fwd: int = 8,
+                 lag_inv: int = 16) -> None:
+    t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv)
+    _call("pm_plan_tune", plan, ctypes.byref(t))
+
+
+PM_FAULT_WITHHOLD_SIGNAL = 1
+
+
+def pm_plan_inject_fault(plan: int, kind: int) -> None:
+    _call("pm_plan_inject_fault", plan, kind)
+
+
+def pm_plan_get_tuning(plan: int) -> PmTuning:
+    t = PmTuning()
+    _call("pm_plan_get_tuning", plan, ctypes.byref(t))
+    return t
 
 
 def pm_plan_sync(plan: int, stream: int = 0) -> None:

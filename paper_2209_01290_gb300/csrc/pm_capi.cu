@@ -86,10 +86,17 @@ struct pm_plan {
   // ordered by the stream).
   struct Scratch {
     cudaStream_t stream;
-    uint64_t* ptr;
+    uint64_t* ptr;      // [units][N] words
     uint64_t units;
+    uint32_t* ctl;      // persistent-kernel control block
+    size_t ctl_words;
   };
   std::vector<Scratch> scratch;
+  // Launch choice for polymul (set by pm_plan_tune / pm_plan_autotune).
+  pm_tuning tune{};
+  // Fault injection for tests (pm_plan_inject_fault): consumed by the next
+  // persistent launch.
+  int inject = 0;
   cudaStream_t side_in = nullptr, side_out = nullptr;
   cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {}, ev_start = nullptr,
               ev_end = nullptr;
@@ -127,14 +134,36 @@ pm_status check_batch(const pm_plan* p, uint32_t npoly) {
 
 // The stream's scratch area, grown to at least `units` polynomials (caller
 // holds p->mu).  Growing frees the old area (cudaFree synchronises the
-// device) and allocates a new one.
-pm_status ensure_scratch(pm_plan* p, cudaStream_t st, uint64_t units, uint64_t** out) {
+// device) and allocates a new one.  With `ctl`, also the persistent kernel's
+// control block for `units` units.
+pm_status ensure_scratch(pm_plan* p, cudaStream_t st, uint64_t units, uint64_t** out,
+                         uint32_t** ctl = nullptr) {
   pm_plan::Scratch* sc = nullptr;
   for (auto& s : p->scratch)
     if (s.stream == st) sc = &s;
   if (!sc) {
-    p->scratch.push_back(pm_plan::Scratch{st, nullptr, 0});
+    p->scratch.push_back(pm_plan::Scratch{st, nullptr, 0, nullptr, 0});
     sc = &p->scratch.back();
+  }
+  if (ctl) {
+    const size_t words = pm::persist_ctl_words((uint32_t)units);
+    if (words > sc->ctl_words) {
+      if (sc->ctl) {
+        cudaError_t e = cudaFree(sc->ctl);
+        sc->ctl = nullptr;
+        sc->ctl_words = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(ctl)");
+      }
+      cudaError_t e = cudaMalloc(&sc->ctl, words * 4);
+      if (e != cudaSuccess) {
+        sc->ctl = nullptr;
+        return cuda_fail(e, "cudaMalloc(ctl)");
+      }
+      e = cudaMemset(sc->ctl, 0, words * 4);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(ctl)");
+      sc->ctl_words = words;
+    }
+    *ctl = sc->ctl;
   }
   if (units > sc->units) {
     if (sc->ptr) {
@@ -161,7 +190,10 @@ void destroy_plan(pm_plan* p) {
   cudaFree(p->d_twf);
   cudaFree(p->d_twi);
   cudaFree(p->d_flag);
-  for (auto& sc : p->scratch) cudaFree(sc.ptr);
+  for (auto& sc : p->scratch) {
+    cudaFree(sc.ptr);
+    cudaFree(sc.ctl);
+  }
   if (p->side_in) cudaStreamDestroy(p->side_in);
   if (p->side_out) cudaStreamDestroy(p->side_out);
   for (int i = 0; i < kHostChunks; ++i) {
@@ -173,17 +205,38 @@ void destroy_plan(pm_plan* p) {
   delete p;
 }
 
+bool use_persistent(const pm_plan* p) {
+  return p->tune.variant == PM_VARIANT_PERSISTENT && p->logn >= 13;
+}
+
 pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
                        uint32_t npoly, cudaStream_t st) {
   pm::KParams P = base_params(p, npoly);
   P.a = d_a;
   P.b = d_b;
   P.c = d_c;
+  const pm::PhaseEvents* pe = p->phase.n ? &p->phase : nullptr;
+  cudaError_t e;
+  if (use_persistent(p)) {
+    uint32_t* ctl = nullptr;
+    pm_status s = ensure_scratch(p, st, P.nunits, &P.s, &ctl);
+    if (s != PM_OK) return s;
+    if (pe && pe->n > 0 && (e = cudaEventRecord(pe->ev[0], st)) != cudaSuccess)
+      return cuda_fail(e, "event");
+    const uint32_t withheld = (p->inject == PM_FAULT_WITHHOLD_SIGNAL) ? 1u : 0u;
+    p->inject = 0;
+    e = pm::launch_polymul_persistent(P, ctl, p->num_sms * (int)p->tune.ctas_per_sm,
+                                      p->tune.lag_fwd, p->tune.lag_inv, st, withheld);
+    if (e != cudaSuccess) return cuda_fail(e, "persistent polymul launch");
+    for (int k = 1; pe && k < pe->n; ++k)
+      if ((e = cudaEventRecord(pe->ev[k], st)) != cudaSuccess) return cuda_fail(e, "event");
+    return PM_OK;
+  }
   if (pm::polymul_needs_scratch(p->logn)) {
     pm_status s = ensure_scratch(p, st, P.nunits, &P.s);
     if (s != PM_OK) return s;
   }
-  cudaError_t e = pm::launch_polymul(P, st, p->phase.n ? &p->phase : nullptr);
+  e = pm::launch_polymul(P, st, pe);
   if (e != cudaSuccess) return cuda_fail(e, "polymul launch");
   return PM_OK;
 }
@@ -268,6 +321,10 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   if (!p) return fail(PM_ERR_OOM, "host allocation failed");
   p->device = device;
   p->flags = flags;
+  p->tune.variant = (log2n >= 13) ? PM_VARIANT_PERSISTENT : PM_VARIANT_SPLIT;
+  p->tune.ctas_per_sm = 3;
+  p->tune.lag_fwd = 8;
+  p->tune.lag_inv = 16;
   p->logn = log2n;
   p->nlimbs = nlimbs;
   p->q.assign(q, q + nlimbs);
@@ -278,6 +335,7 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
   e = prepare_device(device);
+  if (e == cudaSuccess) e = pm::persist_prepare();
   if (e != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "kernel attributes");
@@ -526,12 +584,8 @@ pm_status pm_polymul_host(const pm_plan* plan, const uint64_t* h_a, const uint64
         (e = cudaStreamWaitEvent(st, p->ev_in[k], 0)) != cudaSuccess)
       return cuda_fail(e, "pipeline copy-in");
     // the scratch is indexed from unit 0 of each launch; chunks run in order on `st`
-    pm::KParams P = base_params(p, cnt);
-    P.a = d_a + off;
-    P.b = d_b + off;
-    P.c = d_c + off;
-    P.s = scratch;
-    if ((e = pm::launch_polymul(P, st)) != cudaSuccess) return cuda_fail(e, "polymul launch");
+    (void)scratch;
+    if ((s = polymul_impl(p, d_a + off, d_b + off, d_c + off, cnt, st)) != PM_OK) return s;
     if ((e = cudaEventRecord(p->ev_done[k], st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(p->side_out, p->ev_done[k], 0)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h_c + off, d_c + off, bytes, cudaMemcpyDeviceToHost, p->side_out)) !=
@@ -588,6 +642,51 @@ pm_status pm_plan_sync(const pm_plan* plan, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "device error");
+  // a persistent launch on this stream that gave up waiting leaves a flag
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  for (auto& sc : p->scratch) {
+    if (sc.stream != (cudaStream_t)stream || !sc.ctl) continue;
+    uint32_t flag = 0;
+    if ((e = cudaMemcpy(&flag, sc.ctl + 1, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "read status");
+    if (flag) {
+      cudaMemset(sc.ctl + 1, 0, 4);
+      return fail(PM_ERR_TIMEOUT, "a persistent launch gave up waiting for a dependency");
+    }
+  }
+  return ok();
+}
+
+pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
+  if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
+    return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
+  if (t->variant == PM_VARIANT_PERSISTENT &&
+      (t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->lag_fwd < 1 || t->lag_inv <= t->lag_fwd ||
+       t->lag_inv > 4096))
+    return fail(PM_ERR_ARG, "persistent tuning needs 1 <= ctas_per_sm <= 3, 1 <= lag_fwd < lag_inv <= 4096");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  plan->tune = *t;
+  return ok();
+}
+
+pm_status pm_plan_inject_fault(pm_plan* plan, int kind) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (kind != 0 && kind != PM_FAULT_WITHHOLD_SIGNAL) return fail(PM_ERR_ARG, "unknown fault %d", kind);
+  std::lock_guard<std::mutex> lk(plan->mu);
+  plan->inject = kind;
+  return ok();
+}
+
+pm_status pm_plan_get_tuning(const pm_plan* plan, pm_tuning* t) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
+  *t = plan->tune;
   return ok();
 }
 

@@ -31,6 +31,21 @@ struct PhaseEvents {
   int n;
 };
 
+// Persistent work-queue launch (pm_persist.cu).
+struct PersistArgs {
+  uint32_t* ctl;    // [0] ticket counter, [1] error flag, [4 + 2u] per-unit counters
+  uint32_t F, W, I; // column-forward, row and column-inverse tasks per unit
+  uint32_t lagF;    // ticket groups between a unit's column-forward and row tasks
+  uint32_t lagI;    // ticket groups between a unit's column-forward and column-inverse tasks
+  uint32_t ntasks;  // total tickets
+  uint32_t withheld;  // fault injection: row tasks wait for this many extra signals (0)
+};
+
+cudaError_t persist_prepare();
+size_t persist_ctl_words(uint32_t nunits);
+cudaError_t launch_polymul_persistent(const KParams& P, uint32_t* ctl, int grid, uint32_t lagF,
+                                      uint32_t lagI, cudaStream_t st, uint32_t withheld = 0);
+
 cudaError_t kernels_prepare();
 cudaError_t launch_polymul(const KParams& P, cudaStream_t st,
                            const PhaseEvents* pe = nullptr);

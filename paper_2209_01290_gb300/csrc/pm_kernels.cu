@@ -34,271 +34,9 @@
 
 #include "pm_arith.cuh"
 #include "pm_internal.h"
+#include "pm_passes.cuh"
 
 namespace pm {
-
-constexpr int kRowLog = 12;
-constexpr int kRow = 1 << kRowLog;        // 4096 words per row
-constexpr int kRowPad = kRow + kRow / 32;  // one pad word per 32: conflict-free passes
-
-__device__ __forceinline__ int padj(int j) { return j + (j >> 5); }
-
-// ------------------------------------------------------------------ passes
-
-// Four consecutive merged-CT stages (Algorithm 6) on a register group of 16
-// words.  Global stages s0..s0+3; the group lies in the (N >> s0)-word block
-// number g, its 16 words spaced N >> (s0+4) apart.  Stage s0+st pairs
-// (u, u + 8 >> st) with twiddle Psi_br[2^(s0+st) + g 2^st + (u >> (4-st))].
-// (Stages are template parameters so every register index is a constant.)
-template <int ST>
-__device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                            uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
-  constexpr int h = 8 >> ST;
-  const uint32_t base = (1u << (s0 + ST)) + (g << ST);
-#pragma unroll
-  for (int blk = 0; blk < (1 << ST); blk++) {
-    const TwPair t = ld_tw(tw + base + blk);
-#pragma unroll
-    for (int u0 = 0; u0 < h; u0++)
-      ct_bfly(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
-  }
-}
-
-__device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                     uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
-  ct16_stage1<0>(v, tw, s0, g, q, two_q);
-  ct16_stage1<1>(v, tw, s0, g, q, two_q);
-  ct16_stage1<2>(v, tw, s0, g, q, two_q);
-  ct16_stage1<3>(v, tw, s0, g, q, two_q);
-}
-
-// Four consecutive merged-GS stages (Algorithm 7, 1/2-scaled) on a group of
-// 16 words.  GS stages sig0..sig0+3 (k = 2^sig); the group is block g of
-// 2^(sig0+4) words.  Stage sig0+st pairs (u, u + 2^st) with twiddle
-// Psi^-1_br[(N >> (sig0+st+1)) + g 2^(3-st) + (u >> (st+1))] (times 1/2).
-template <int ST, bool HALVE>
-__device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                           uint32_t logn, uint32_t sig0, uint32_t g,
-                                           uint64_t q, uint64_t two_q, uint64_t hq) {
-  constexpr int h = 1 << ST;
-  const uint32_t base = (1u << (logn - sig0 - ST - 1)) + (g << (3 - ST));
-#pragma unroll
-  for (int blk = 0; blk < (8 >> ST); blk++) {
-    const TwPair t = ld_tw(tw + base + blk);
-#pragma unroll
-    for (int u0 = 0; u0 < h; u0++)
-      gs_bfly_mode<HALVE>(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
-  }
-}
-
-template <bool HALVE>
-__device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                     uint32_t logn, uint32_t sig0, uint32_t g,
-                                     uint64_t q, uint64_t two_q, uint64_t hq) {
-  gs16_stage<0, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<1, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<2, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
-  gs16_stage<3, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
-}
-
-// Merged CT on a column of R words (the first log2 R stages of the N-point
-// transform): stage s pairs (t, t + R >> (s+1)) with twiddle Psi_br[2^s + blk].
-template <int R, int S>
-__device__ __forceinline__ void ct_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                             uint64_t q, uint64_t two_q) {
-  if constexpr ((1 << S) < R) {
-    constexpr int h = R >> (S + 1);
-#pragma unroll
-    for (int blk = 0; blk < (1 << S); blk++) {
-      const TwPair t = ld_tw(tw + (1u << S) + blk);
-#pragma unroll
-      for (int u0 = 0; u0 < h; u0++)
-        ct_bfly(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
-    }
-    ct_col_stage<R, S + 1>(x, tw, q, two_q);
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void ct_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                       uint64_t q, uint64_t two_q) {
-  ct_col_stage<R, 0>(x, tw, q, two_q);
-}
-
-// Merged GS on a column of R words (the last log2 R stages): the GS stage
-// with k = 4096 * 2^E pairs (t, t + 2^E) with twiddle
-// Psi^-1_br[(R >> (E+1)) + (t >> (E+1))].  Without per-stage halving the
-// final stage (2^E = R/2, the transform's last) folds in 1/N.
-template <int R, int E, bool HALVE>
-__device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                             const LimbConst& K) {
-  if constexpr ((1 << E) < R) {
-    constexpr int h = 1 << E;
-    if constexpr (!HALVE && 2 * h == R) {
-#pragma unroll
-      for (int u0 = 0; u0 < h; u0++) gs_bfly_last(x[u0], x[u0 + h], K);
-    } else {
-#pragma unroll
-      for (int blk = 0; blk < R / (2 * h); blk++) {
-        const TwPair t = ld_tw(tw + (R >> (E + 1)) + blk);
-#pragma unroll
-        for (int u0 = 0; u0 < h; u0++)
-          gs_bfly_mode<HALVE>(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, K.q,
-                              K.two_q, K.half_q1);
-      }
-    }
-    gs_col_stage<R, E + 1, HALVE>(x, tw, K);
-  }
-}
-
-template <int R, bool HALVE>
-__device__ __forceinline__ void gs_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                       const LimbConst& K) {
-  gs_col_stage<R, 0, HALVE>(x, tw, K);
-}
-
-__device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
-  LimbConst k;
-  const ulonglong2* s = reinterpret_cast<const ulonglong2*>(p);
-  const ulonglong2 v0 = __ldg(s), v1 = __ldg(s + 1), v2 = __ldg(s + 2), v3 = __ldg(s + 3),
-                   v4 = __ldg(s + 4);
-  k.q = v0.x;
-  k.two_q = v0.y;
-  k.half_q1 = v1.x;
-  k.mu = v1.y;
-  k.m = (uint32_t)v2.x;
-  k.sh1 = (uint32_t)(v2.x >> 32);
-  k.sh2 = (uint32_t)v2.y;
-  k.halving = (uint32_t)(v2.y >> 32);
-  k.ninv = v3.x;
-  k.ninv_p = v3.y;
-  k.w1ninv = v4.x;
-  k.w1ninv_p = v4.y;
-  return k;
-}
-
-// ----------------------------------------------------------- row pipeline
-
-// The 12 in-row stages of one 4096-word row (row t of a unit of 2^logn
-// words) as three radix-16 passes; 256 threads per row.  Each pass reads 16
-// words per thread, runs 4 stages in registers and writes them back.  The
-// three thread->word layouts
-//   layout 0: j = th + 256 u                      (CT stages n-12.., GS 8..11)
-//   layout 1: j = 256 (th>>4) + (th&15) + 16 u    (CT stages n-8..,  GS 4..7)
-//   layout 2: j = 16 th + u                       (CT stages n-4..,  GS 0..3)
-// are all bank-conflict free with the 1-in-32 padding.  The pass loop is
-// not unrolled: one copy of the radix-16 body serves all passes, which keeps
-// the kernel small enough for the instruction cache.
-struct PassGeo {
-  int layout;    // 0, 1 or 2
-  int pbase;     // padded smem index of u = 0
-  uint32_t g;    // block index of the group within the whole transform
-};
-
-// With the 1-in-32 padding p(j) = j + (j >> 5), the padded index of word u
-// of a group is pbase + off(u) with a compile-time offset per layout:
-//   layout 0: 264 u;  layout 1: 16 u + (u >> 1);  layout 2: u.
-template <int L>
-__device__ __forceinline__ constexpr int lay_off(int u) {
-  return L == 0 ? 264 * u : (L == 1 ? 16 * u + (u >> 1) : u);
-}
-
-__device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
-  PassGeo G;
-  G.layout = layout;
-  if (layout == 0) {
-    G.pbase = th + (th >> 5);
-    G.g = t;
-  } else if (layout == 1) {
-    G.pbase = 264 * (th >> 4) + (th & 15);
-    G.g = t * 16 + (th >> 4);
-  } else {
-    G.pbase = 16 * th + (th >> 1);
-    G.g = t * 256 + th;
-  }
-  return G;
-}
-
-template <int L>
-__device__ __forceinline__ void ld16(uint64_t (&v)[16], const uint64_t* s) {
-#pragma unroll
-  for (int u = 0; u < 16; u++) v[u] = s[lay_off<L>(u)];
-}
-
-template <int L>
-__device__ __forceinline__ void st16(uint64_t* s, const uint64_t (&v)[16]) {
-#pragma unroll
-  for (int u = 0; u < 16; u++) s[lay_off<L>(u)] = v[u];
-}
-
-__device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
-  const uint64_t* p = s + G.pbase;
-  if (G.layout == 0) ld16<0>(v, p);
-  else if (G.layout == 1) ld16<1>(v, p);
-  else ld16<2>(v, p);
-}
-
-__device__ __forceinline__ void st_smem16(uint64_t* s, const PassGeo& G, const uint64_t (&v)[16]) {
-  uint64_t* p = s + G.pbase;
-  if (G.layout == 0) st16<0>(p, v);
-  else if (G.layout == 1) st16<1>(p, v);
-  else st16<2>(p, v);
-}
-
-// Forward in-row stages of one operand.  Source: global row `g_src` (layout
-// 0, coalesced) or, if null, the smem row `s` (already holding the row).
-// Leaves the last pass's 16 words (layout 2, lazy [0,4q)) in v.
-__device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_src, uint64_t* s,
-                                         const TwPair* __restrict__ twf, uint32_t logn,
-                                         uint32_t t, int th, uint64_t q, uint64_t two_q) {
-#pragma unroll 1
-  for (int p = 0; p < 3; p++) {
-    const PassGeo G = pass_geo(p, th, t);
-    if (p == 0 && g_src) {
-#pragma unroll
-      for (int u = 0; u < 16; u++) v[u] = __ldcs(g_src + th + 256 * u);
-    } else {
-      ld_smem16(v, s, G);
-    }
-    ct16(v, twf, logn - 12 + 4 * p, G.g, q, two_q);
-    if (p < 2) {
-      st_smem16(s, G, v);
-      __syncthreads();
-    }
-  }
-}
-
-// Inverse in-row stages (1/2-scaled).  v holds layout-2 words on entry.
-// The last pass writes layout 0 either to the global row `g_dst`
-// (canonical if `final`) or, if null, back to smem.
-// With `final` (the row is the whole transform, N = 4096) and no per-stage
-// halving, the outputs are multiplied by N^-1 before the store.
-template <bool HALVE>
-__device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, bool final,
-                                         uint64_t* s, const TwPair* __restrict__ twi,
-                                         uint32_t logn, uint32_t t, int th, const LimbConst& K) {
-  const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
-#pragma unroll 1
-  for (int p = 0; p < 3; p++) {
-    const PassGeo G = pass_geo(2 - p, th, t);
-    if (p > 0) ld_smem16(v, s, G);
-    gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq);
-    if (p < 2) {
-      st_smem16(s, G, v);
-      __syncthreads();
-    }
-  }
-  if (g_dst) {
-    if (!HALVE && final) {
-#pragma unroll
-      for (int u = 0; u < 16; u++) v[u] = mul_shoup_lazy(v[u], K.ninv, K.ninv_p, q);
-    }
-#pragma unroll
-    for (int u = 0; u < 16; u++) __stcs(g_dst + th + 256 * u, final ? csub(v[u], q) : v[u]);
-  } else {
-    st_smem16(s, pass_geo(0, th, t), v);
-  }
-}
 
 // ------------------------------------------------------------------ kernels
 
@@ -340,20 +78,9 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
       __stcs(dst + u / 2, make_ulonglong2(reduce4(v[u], K.q, K.two_q),
                                           reduce4(v[u + 1], K.q, K.two_q)));
   } else {
-    const uint64_t* ga = (single ? P.a : P.c) + off;
-    const uint64_t* gb = (single ? P.b : P.s) + off;
-    // operand a: keep its transform in smem (layout 2) while b is done
-    rows_fwd(v, ga, sa, twf, logn, t, th, K.q, K.two_q);
-    const PassGeo G2 = pass_geo(2, th, t);
-    st_smem16(sa, G2, v);
-    rows_fwd(v, gb, sb, twf, logn, t, th, K.q, K.two_q);
-    // pointwise product (Algorithm 4) in bit-reversed order
-#pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
-      v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
-    }
-    rows_inv<HALVE>(v, P.c + off, single, sa, twi, logn, t, th, K);
+    (void)sb;
+    row_task_polymul<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
+                                   P.c + off, single, smem, twf, twi, K, logn, t);
   }
 }
 

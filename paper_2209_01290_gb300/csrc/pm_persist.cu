@@ -1,0 +1,321 @@
+// pm_persist.cu -- one persistent launch for a whole batch of negacyclic
+// products (arxiv 2209.01290, Eq. 2, batched over RNS limbs and polynomials
+// like the paper's throughput-oriented TOM-NTT, Sec. V-C).
+//
+// The column-split path (N = R * 4096) has three kinds of work per unit:
+//   F column-forward tasks (256 columns of one operand each, the first
+//     log2 R stages of Algorithm 6),
+//   W = R row tasks (the 12 in-row forward stages of a and b, the
+//     Algorithm 4 pointwise product, the 12 in-row inverse stages),
+//   I = 16 column-inverse tasks (the last log2 R stages of Algorithm 7 and
+//     the reduction to [0, q)).
+// Instead of three launches, a grid of CTAs that stays resident takes
+// tickets from a global counter in a fixed software-pipelined order: ticket
+// group g holds the column-forward tasks of unit g, the row tasks of unit
+// g - lagF and the column-inverse tasks of unit g - lagI.  Memory-bound
+// column work of one unit therefore runs on the SMs at the same time as the
+// compute-bound row work of others, and each unit's intermediate image is
+// read back a few groups after it was written, while it is still in L2.
+//
+// A row task waits until all column-forward tasks of its unit are done, a
+// column-inverse task until all its unit's rows are done (per-unit counters,
+// release/acquire at GPU scope).  Tickets are handed out in order and a
+// task only ever waits for tasks with smaller tickets, which were taken by
+// running CTAs, so every wait ends; each wait is still bounded (about a
+// second), after which the CTA records PM_ERR_TIMEOUT in the control block
+// and carries on.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pm_arith.cuh"
+#include "pm_internal.h"
+#include "pm_passes.cuh"
+
+namespace pm {
+
+namespace {
+
+constexpr int kTaskCols = 256;        // columns per column task (one per thread)
+constexpr uint64_t kWaitNs = 1000000000ull;  // give up a wait after one second
+constexpr long kWaitIters = 1L << 26;        // backstop on the number of polls
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits until *ctr >= target, for at most about a second; on
+// giving up it sets the error flag and the CTA proceeds (its result is then
+// invalid, which the host learns from the flag).
+__device__ __forceinline__ void cta_wait(const uint32_t* ctr, uint32_t target, int* err) {
+  if (threadIdx.x == 0 && ld_acquire(ctr) < target) {
+    const uint64_t t0 = global_ns();
+    long it = 0;
+    while (ld_acquire(ctr) < target) {
+      if (++it > kWaitIters || global_ns() - t0 > kWaitNs) {
+        atomicOr(err, 1);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncthreads();
+}
+
+// All threads' global writes are complete; thread 0 publishes them.
+__device__ __forceinline__ void cta_signal(uint32_t* ctr) {
+  __syncthreads();
+  if (threadIdx.x == 0) red_release_add(ctr, 1);
+}
+
+// Column-forward task, R <= 16: thread = one column of one operand.
+template <int R>
+__device__ __forceinline__ void colf_regs(const uint64_t* src, uint64_t* dst,
+                                          const TwPair* __restrict__ twf, const LimbConst& K) {
+  uint64_t x[R];
+#pragma unroll
+  for (int t = 0; t < R; t++) x[t] = __ldcg(src + (size_t)t * kRow);
+  ct_col<R>(x, twf, K.q, K.two_q);
+#pragma unroll
+  for (int t = 0; t < R; t++) dst[(size_t)t * kRow] = x[t];
+}
+
+// Column-forward task, R = 32: the column is parked in smem (stride 256,
+// private to the thread) between the first stage (pairs t, t+16) and the
+// radix-16 groups of the two halves (stages 1..4, block index = half).
+__device__ __forceinline__ void colf_32(const uint64_t* src, uint64_t* dst, uint64_t* sm,
+                                        const TwPair* __restrict__ twf, const LimbConst& K) {
+  const int th = threadIdx.x;
+  const TwPair w = ld_tw(twf + 1);
+#pragma unroll 1
+  for (int b = 0; b < 2; b++) {
+    uint64_t lo[8], hi[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      lo[i] = __ldcg(src + (size_t)(8 * b + i) * kRow);
+      hi[i] = __ldcg(src + (size_t)(8 * b + i + 16) * kRow);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      ct_bfly(lo[i], hi[i], w.w, w.wp, K.q, K.two_q);
+      sm[(8 * b + i) * kTaskCols + th] = lo[i];
+      sm[(8 * b + i + 16) * kTaskCols + th] = hi[i];
+    }
+  }
+#pragma unroll 1
+  for (int h = 0; h < 2; h++) {
+    uint64_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = sm[(16 * h + u) * kTaskCols + th];
+    ct16(v, twf, 1, h, K.q, K.two_q);
+#pragma unroll
+    for (int u = 0; u < 16; u++) dst[(size_t)(16 * h + u) * kRow] = v[u];
+  }
+}
+
+// Column-inverse task, R <= 16: thread = one column of c'.
+template <int R, bool HALVE>
+__device__ __forceinline__ void coli_regs(uint64_t* p, const TwPair* __restrict__ twi,
+                                          const LimbConst& K) {
+  uint64_t x[R];
+#pragma unroll
+  for (int t = 0; t < R; t++) x[t] = __ldcg(p + (size_t)t * kRow);
+  gs_col<R, HALVE>(x, twi, K);
+#pragma unroll
+  for (int t = 0; t < R; t++) __stcs(p + (size_t)t * kRow, csub(x[t], K.q));
+}
+
+// Column-inverse task, R = 32: radix-16 GS groups on the two halves (GS
+// stages with k = 4096 * 2^e, e = 0..3, viewed as a 32-point transform), then
+// the last stage (pairs t, t+16, twiddle Psi^-1_br[1]) and the reduction.
+template <bool HALVE>
+__device__ __forceinline__ void coli_32(uint64_t* p, uint64_t* sm, const TwPair* __restrict__ twi,
+                                        const LimbConst& K) {
+  const int th = threadIdx.x;
+#pragma unroll 1
+  for (int h = 0; h < 2; h++) {
+    uint64_t v[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = __ldcg(p + (size_t)(16 * h + u) * kRow);
+    gs16<HALVE>(v, twi, 5, 0, h, K.q, K.two_q, K.half_q1);
+#pragma unroll
+    for (int u = 0; u < 16; u++) sm[(16 * h + u) * kTaskCols + th] = v[u];
+  }
+  const TwPair w = ld_tw(twi + 1);
+#pragma unroll 1
+  for (int b = 0; b < 2; b++) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      uint64_t x0 = sm[(8 * b + i) * kTaskCols + th], x1 = sm[(8 * b + i + 16) * kTaskCols + th];
+      if constexpr (HALVE)
+        gs_bfly_half(x0, x1, w.w, w.wp, K.q, K.two_q, K.half_q1);
+      else
+        gs_bfly_last(x0, x1, K);
+      __stcs(p + (size_t)(8 * b + i) * kRow, csub(x0, K.q));
+      __stcs(p + (size_t)(8 * b + i + 16) * kRow, csub(x1, K.q));
+    }
+  }
+}
+
+template <int R, bool HALVE>
+__device__ void run_task(const KParams& P, const PersistArgs& A, uint32_t ticket, uint64_t* smem) {
+  const uint32_t logn = P.logn;
+  const uint32_t GS = A.F + A.W + A.I;
+  const uint32_t g = ticket / GS;
+  uint32_t r = ticket - g * GS;
+  uint32_t* done = A.ctl + 4;  // [unit][2]: column-forward tasks done, rows done
+  int* err = reinterpret_cast<int*>(A.ctl + 1);
+  if (r < A.F) {  // ---- column forward, unit g
+    const uint32_t unit = g;
+    if (unit >= P.nunits) return;
+    const uint32_t op = r / (kRow / kTaskCols), cs = r % (kRow / kTaskCols);
+    const uint32_t limb = unit % P.nlimbs;
+    const LimbConst K = ld_limb(P.lc + limb);
+    const TwPair* twf = P.twf + ((size_t)limb << logn);
+    const size_t off = ((size_t)unit << logn) + cs * kTaskCols + threadIdx.x;
+    const uint64_t* src = (op == 0 ? P.a : P.b) + off;
+    uint64_t* dst = (op == 0 ? P.c : P.s) + off;
+    if constexpr (R == 32)
+      colf_32(src, dst, smem, twf, K);
+    else
+      colf_regs<R>(src, dst, twf, K);
+    cta_signal(done + 2 * unit);
+    return;
+  }
+  r -= A.F;
+  if (r < A.W) {  // ---- row r of unit g - lagF
+    if (g < A.lagF || g - A.lagF >= P.nunits) return;
+    const uint32_t unit = g - A.lagF;
+    if (A.F) cta_wait(done + 2 * unit, A.F + A.withheld, err);
+    const uint32_t limb = unit % P.nlimbs;
+    const LimbConst K = ld_limb(P.lc + limb);
+    const TwPair* twf = P.twf + ((size_t)limb << logn);
+    const TwPair* twi = P.twi + ((size_t)limb << logn);
+    const size_t off = ((size_t)unit << logn) + (size_t)r * kRow;
+    const bool single = (logn == kRowLog);
+    row_task_polymul<HALVE, true>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
+                                  P.c + off, single, smem, twf, twi, K, logn, r);
+    if (A.I) cta_signal(done + 2 * unit + 1);
+    return;
+  }
+  r -= A.W;
+  // ---- column inverse, unit g - lagI
+  if (g < A.lagI || g - A.lagI >= P.nunits) return;
+  const uint32_t unit = g - A.lagI;
+  cta_wait(done + 2 * unit + 1, A.W, err);
+  const uint32_t limb = unit % P.nlimbs;
+  const LimbConst K = ld_limb(P.lc + limb);
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  uint64_t* p = P.c + ((size_t)unit << logn) + r * kTaskCols + threadIdx.x;
+  if constexpr (R == 32)
+    coli_32<HALVE>(p, smem, twi, K);
+  else
+    coli_regs<R, HALVE>(p, twi, K);
+}
+
+}  // namespace
+
+template <int R, bool HALVE>
+__global__ void __launch_bounds__(256, 3) k_persist(KParams P, PersistArgs A) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  __shared__ uint32_t s_ticket;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(A.ctl, 1u);
+    __syncthreads();
+    const uint32_t ticket = s_ticket;
+    __syncthreads();  // everyone has read s_ticket before thread 0 rewrites it
+    if (ticket >= A.ntasks) break;
+    run_task<R, HALVE>(P, A, ticket, smem);
+    __syncthreads();  // smem reuse by the next task
+  }
+}
+
+namespace {
+
+constexpr int kPersistSmem = 2 * kRowPad * 8;
+
+template <int R>
+cudaError_t launch_r(const KParams& P, const PersistArgs& A, int grid, cudaStream_t st) {
+  if (P.halving)
+    k_persist<R, true><<<grid, 256, kPersistSmem, st>>>(P, A);
+  else
+    k_persist<R, false><<<grid, 256, kPersistSmem, st>>>(P, A);
+  return cudaGetLastError();
+}
+
+template <int R, bool H>
+cudaError_t set_attr() {
+  return cudaFuncSetAttribute((const void*)k_persist<R, H>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+}
+
+}  // namespace
+
+cudaError_t persist_prepare() {
+  cudaError_t e = cudaSuccess;
+  if ((e = set_attr<1, false>()) || (e = set_attr<1, true>()) || (e = set_attr<2, false>()) ||
+      (e = set_attr<2, true>()) || (e = set_attr<4, false>()) || (e = set_attr<4, true>()) ||
+      (e = set_attr<8, false>()) || (e = set_attr<8, true>()) || (e = set_attr<16, false>()) ||
+      (e = set_attr<16, true>()) || (e = set_attr<32, false>()) || (e = set_attr<32, true>()))
+    return e;
+  return cudaSuccess;
+}
+
+size_t persist_ctl_words(uint32_t nunits) { return 4 + 2 * (size_t)nunits; }
+
+// Launch the persistent polymul for N >= 4096.  `ctl` is a zeroed control
+// block of persist_ctl_words(nunits) words.  P.a/P.b/P.c/P.s follow the same
+// aliasing rules as the column-split path (see launch_polymul).
+cudaError_t launch_polymul_persistent(const KParams& P0, uint32_t* ctl, int grid, uint32_t lagF,
+                                      uint32_t lagI, cudaStream_t st, uint32_t withheld) {
+  if (P0.nunits == 0) return cudaSuccess;
+  if (P0.logn < 12 || P0.logn > 17) return cudaErrorInvalidValue;
+  KParams P = P0;
+  int nops = 2;
+  if (P.logn > 12) {
+    if (P.a == P.b) {
+      P.b = nullptr;
+      P.s = P.c;
+      nops = 1;
+    } else if (P.c == P.b) {
+      const uint64_t* t = P.a;
+      P.a = P.b;
+      P.b = t;
+    }
+  }
+  PersistArgs A{};
+  A.ctl = ctl;
+  const uint32_t R = 1u << (P.logn - kRowLog);
+  A.F = (P.logn > 12) ? (uint32_t)nops * (kRow / kTaskCols) : 0;
+  A.W = R;
+  A.I = (P.logn > 12) ? (kRow / kTaskCols) : 0;
+  A.lagF = A.F ? lagF : 0;
+  A.lagI = A.I ? (lagI > A.lagF ? lagI : A.lagF + 1) : A.lagF;
+  A.ntasks = (P.nunits + A.lagI) * (A.F + A.W + A.I);
+  A.withheld = A.F ? withheld : 0;
+  cudaError_t e = cudaMemsetAsync(ctl, 0, persist_ctl_words(P.nunits) * 4, st);
+  if (e != cudaSuccess) return e;
+  switch (R) {
+    case 1: return launch_r<1>(P, A, grid, st);
+    case 2: return launch_r<2>(P, A, grid, st);
+    case 4: return launch_r<4>(P, A, grid, st);
+    case 8: return launch_r<8>(P, A, grid, st);
+    case 16: return launch_r<16>(P, A, grid, st);
+    case 32: return launch_r<32>(P, A, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pm

@@ -20,21 +20,26 @@ def torch_cuda():
     return torch
 
 
-def _plan(log2n, nlimbs, qbits=60, halving=False):
+def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None):
     from paper_2209_01290_gb300 import Plan, capi
     qs, psis = capi.pm_find_params(log2n, nlimbs, qbits)
-    return Plan(1 << log2n, qs, psis, halving=halving), qs, psis
+    plan = Plan(1 << log2n, qs, psis, halving=halving)
+    if variant is not None:
+        capi.pm_plan_tune(plan.handle, variant)
+    return plan, qs, psis
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["split", "persistent"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold1N", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
-def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving):
+def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving, variant):
     """Every code path: radix-2 smem kernel (N <= 2^11), single-row kernel
-    (2^12), one-CTA 2^13 kernel, column split (2^14..2^17); 2 polys x 3 limbs;
+    (2^12), one-CTA 2^13 kernel, column split (2^14..2^17) as three launches
+    or as one persistent work-queue launch (2^13..2^17); 2 polys x 3 limbs;
     1/N folded into the last stage or applied as per-stage halving."""
     n = 1 << log2n
     L, P = (3, 2) if log2n <= 15 else (2, 1)
-    plan, qs, psis = _plan(log2n, L, halving=halving)
+    plan, qs, psis = _plan(log2n, L, halving=halving, variant=variant)
     a, b = operands(1000 + log2n, qs, P, n)
     want = oracle_polymul_batch(oracle, a, b, qs, psis)
     got = to_host(plan.polymul(to_dev(a), to_dev(b)))

@@ -1,0 +1,70 @@
+"""The persistent work-queue polymul: many units, pipeline lags, tuning
+checks, and the bounded-wait error path (a dependency signal withheld on the
+host side; the waits run out, the host reads PM_ERR_TIMEOUT, later calls
+work)."""
+import numpy as np
+import pytest
+
+from helpers import operands, oracle_polymul_batch, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(log2n, L, P, seed):
+    from paper_2209_01290_gb300 import Plan, capi
+    qs, psis = capi.pm_find_params(log2n, L, 60)
+    plan = Plan(1 << log2n, qs, psis)
+    a, b = operands(seed, qs, P, 1 << log2n)
+    return plan, qs, psis, a, b
+
+
+@pytest.mark.parametrize("log2n,L,P", [(13, 4, 16), (14, 3, 8), (15, 2, 8), (16, 4, 6), (17, 2, 3)])
+@pytest.mark.parametrize("lags", [(1, 2), (8, 16), (40, 90)])
+def test_persistent_lags(oracle, log2n, L, P, lags):
+    """Results do not depend on the pipeline distances or on the CTA count;
+    every unit is checked against the oracle (units > lag exercise the
+    steady state, units < lag the prologue/epilogue)."""
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis, a, b = _setup(log2n, L, P, 11000 + log2n)
+    want = oracle_polymul_batch(oracle, a, b, qs, psis)
+    for ctas in (1, 3):
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT, ctas, lags[0], lags[1])
+        got = to_host(plan.polymul(to_dev(a), to_dev(b)))
+        plan.sync()
+        assert np.array_equal(got, want), (ctas, lags)
+
+
+def test_tuning_validation():
+    from paper_2209_01290_gb300 import capi
+    plan, *_ = _setup(14, 1, 1, 1)
+    t = capi.pm_plan_get_tuning(plan.handle)
+    assert t.variant == capi.PM_VARIANT_PERSISTENT and t.ctas_per_sm == 3
+    for bad in [(capi.PM_VARIANT_PERSISTENT, 0, 8, 16), (capi.PM_VARIANT_PERSISTENT, 3, 8, 8),
+                (capi.PM_VARIANT_PERSISTENT, 4, 8, 16), (7, 3, 8, 16)]:
+        with pytest.raises(capi.PMError) as e:
+            capi.pm_plan_tune(plan.handle, *bad)
+        assert e.value.status == -1
+    capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT)
+    assert capi.pm_plan_get_tuning(plan.handle).variant == capi.PM_VARIANT_SPLIT
+
+
+def test_withheld_signal_times_out_then_recovers(oracle):
+    """Host-side fault injection: the row tasks of the next launch wait for a
+    signal that never comes.  Each wait gives up after about a second, the
+    launch ends, pm_plan_sync reports PM_ERR_TIMEOUT; the next call is
+    correct and reports no error."""
+    import time
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis, a, b = _setup(14, 1, 2, 12000)
+    want = oracle_polymul_batch(oracle, a, b, qs, psis)
+    da, db = to_dev(a), to_dev(b)
+    capi.pm_plan_inject_fault(plan.handle, capi.PM_FAULT_WITHHOLD_SIGNAL)
+    t0 = time.time()
+    plan.polymul(da, db)
+    with pytest.raises(capi.PMError) as e:
+        plan.sync()
+    assert e.value.status == -7
+    assert time.time() - t0 < 30
+    got = to_host(plan.polymul(da, db))
+    plan.sync()
+    assert np.array_equal(got, want)
