@@ -219,6 +219,13 @@ def run_gpu(args):
     stream.synchronize()
 
     peak_mulmod, peak_imad = capi.pm_measure_peaks(dev)
+    if args.variant == "split":
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT)
+    elif args.variant == "persistent":
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT, args.ctas_per_sm,
+                          args.lag_fwd, args.lag_inv)
+    tuning = capi.pm_plan_get_tuning(plan.handle)
+    persistent = tuning.variant == capi.PM_VARIANT_PERSISTENT and log2n >= 13
 
     # ---- warm-up
     for _ in range(args.warmup):
@@ -226,7 +233,7 @@ def run_gpu(args):
     stream.synchronize()
 
     # per-step phase events (recorded by the library on `stream`)
-    nphase = 4 if log2n >= 14 else 2
+    nphase = 4 if (log2n >= 14 and not persistent) else 2
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nphase)] for _ in range(args.steps)]
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for e in [x for row in ev for x in row] + [start, end]:
@@ -276,7 +283,10 @@ def run_gpu(args):
         e2e_value = ws * units / (float(t.item()) / e2e_steps)
 
     # ---- roofline: the dominant kernel (rows, or the single fused kernel)
-    if log2n >= 14:
+    if persistent:
+        dom_idx, dom_name = 0, "k_persist (whole polymul, one persistent launch)"
+        dom_mulmods = mulmods_per_polymul(log2n) * units
+    elif log2n >= 14:
         dom_idx, dom_name = 1, "k_rows<POLYMUL> (in-row stages + Barrett pointwise)"
         dom_mulmods = rows_kernel_mulmods(log2n) * units
     else:
@@ -297,10 +307,11 @@ def run_gpu(args):
                    "N": n, "limbs": L, "products_per_step": units,
                    "operand_bytes_per_step": units * n * 8 * 3,
                    "l2": "inputs (%.2f GiB) larger than L2, no flush" % (units * n * 16 / 2**30),
-                   "parallelism": f"replicas x{ws}"},
-        "gpu_launches": (3 if log2n >= 14 else 1) * args.steps,
+                   "parallelism": f"replicas x{ws}",
+                   "launch": tuning.as_dict()},
+        "gpu_launches": (3 if (log2n >= 14 and not persistent) else 1) * args.steps,
         "phase_ms": {"col_fwd": avg_phase[0], "rows": avg_phase[1], "col_inv": avg_phase[2]}
-        if log2n >= 14 else {"fused": avg_phase[0]},
+        if nphase == 4 else {"single_launch": avg_phase[0]},
         "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12,
                      "peak": peak_mulmod / 1e12, "unit": "Tmulmod/s",
                      "frac": achieved / peak_mulmod, "traffic": None,
@@ -334,6 +345,10 @@ def main():
     ap.add_argument("--batch", type=int, default=1024, help="products per step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
+    ap.add_argument("--ctas-per-sm", type=int, default=3)
+    ap.add_argument("--lag-fwd", type=int, default=8)
+    ap.add_argument("--lag-inv", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
