@@ -192,13 +192,17 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  *                           the pipeline distances in units, ctas_per_sm the
  *                           resident CTAs per SM).  Uses a control block of
  *                           16 + 8 * units bytes in the stream's scratch.
- * The default is PERSISTENT with 3 CTAs per SM, lags 8 and 16. */
+ * row_ops (SPLIT only): 1 = the row kernel transforms a then b (3 CTAs per
+ * SM), 2 = both together sharing twiddle loads (2 CTAs per SM).
+ * pm_plan_autotune() picks these by timing; without it a plan uses SPLIT,
+ * row_ops 1 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
 enum { PM_VARIANT_SPLIT = 0, PM_VARIANT_PERSISTENT = 1 };
 typedef struct pm_tuning {
     int32_t variant;
     uint32_t ctas_per_sm;
     uint32_t lag_fwd;
     uint32_t lag_inv;
+    uint32_t row_ops;
 } pm_tuning;
 
 /* Set / read the plan's launch choice.  PM_ERR_ARG for out-of-range values. */

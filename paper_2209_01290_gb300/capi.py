@@ -190,17 +190,18 @@ PM_VARIANT_PERSISTENT = 1
 
 class PmTuning(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("ctas_per_sm", ctypes.c_uint32),
-                ("lag_fwd", ctypes.c_uint32), ("lag_inv", ctypes.c_uint32)]
+                ("lag_fwd", ctypes.c_uint32), ("lag_inv", ctypes.c_uint32),
+                ("row_ops", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"variant": "persistent" if self.variant == PM_VARIANT_PERSISTENT else "split",
                 "ctas_per_sm": self.ctas_per_sm, "lag_fwd": self.lag_fwd,
-                "lag_inv": self.lag_inv}
+                "lag_inv": self.lag_inv, "row_ops": self.row_ops}
 
 
 def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 3, lag_fwd: int = 8,
-                 lag_inv: int = 16) -> None:
-    t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv)
+                 lag_inv: int = 64, row_ops: int = 1) -> None:
+    t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv, row_ops)
     _call("pm_plan_tune", plan, ctypes.byref(t))
 
 

@@ -121,6 +121,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.nlimbs = p->nlimbs;
   P.nunits = npoly * p->nlimbs;
   P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
+  P.row_ops = p->tune.row_ops == 2 ? 2 : 1;
   return P;
 }
 
@@ -321,10 +322,11 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   if (!p) return fail(PM_ERR_OOM, "host allocation failed");
   p->device = device;
   p->flags = flags;
-  p->tune.variant = (log2n >= 13) ? PM_VARIANT_PERSISTENT : PM_VARIANT_SPLIT;
+  p->tune.variant = PM_VARIANT_SPLIT;
   p->tune.ctas_per_sm = 3;
   p->tune.lag_fwd = 8;
-  p->tune.lag_inv = 16;
+  p->tune.lag_inv = 64;
+  p->tune.row_ops = 1;
   p->logn = log2n;
   p->nlimbs = nlimbs;
   p->q.assign(q, q + nlimbs);
@@ -664,6 +666,7 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
   if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
     return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
+  if (t->row_ops != 1 && t->row_ops != 2) return fail(PM_ERR_ARG, "row_ops must be 1 or 2");
   if (t->variant == PM_VARIANT_PERSISTENT &&
       (t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->lag_fwd < 1 || t->lag_inv <= t->lag_fwd ||
        t->lag_inv > 4096))

@@ -22,6 +22,8 @@ struct KParams {
   uint32_t nlimbs;
   uint32_t nunits;       // npoly * nlimbs
   uint32_t halving;      // 1: per-stage 1/2 scaling (table holds w/2); 0: 1/N folded at the end
+  uint32_t row_ops;      // polymul row kernel: 1 = operands one after the other, 2 = together
+  uint32_t pad;
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the

@@ -84,52 +84,122 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
   }
 }
 
-// Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
-// operand, column); loads the R words {c + 4096 t}, runs the first log2 R
-// stages of Algorithm 6, stores them back in place (to `dst`).
-// For polymul, operand 0 (a) goes to c and operand 1 (b) to the scratch s.
-template <int R>
-__global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+// Polymul rows with a and b transformed together in registers (shared
+// twiddle loads, half the barriers per word; 2 CTAs per SM).
+template <bool HALVE>
+__global__ void __launch_bounds__(256, 2) k_rows2(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t logn = P.logn;
-  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t col = (uint32_t)(gid & (kRow - 1));
-  const size_t rest = gid >> kRowLog;
-  const uint32_t op = (uint32_t)(rest % nops);
-  const uint32_t unit = (uint32_t)(rest / nops);
+  const uint32_t unit = blockIdx.x >> (logn - kRowLog);
+  const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
   if (unit >= P.nunits) return;
   const uint32_t limb = unit % P.nlimbs;
   const LimbConst K = ld_limb(P.lc + limb);
   const TwPair* twf = P.twf + ((size_t)limb << logn);
-  const size_t off = ((size_t)unit << logn) + col;
-  const uint64_t* src = (op == 0 ? P.a : P.b) + off;
-  uint64_t* dst = (op == 0 ? P.c : P.s) + off;
-  uint64_t x[R];
-#pragma unroll
-  for (int t = 0; t < R; t++) x[t] = __ldcs(src + (size_t)t * kRow);
-  ct_col<R>(x, twf, K.q, K.two_q);
-#pragma unroll
-  for (int t = 0; t < R; t++) dst[(size_t)t * kRow] = x[t];
+  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
+  const bool single = (logn == kRowLog);
+  row_task_polymul2<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
+                                  P.c + off, single, smem, twf, twi, K, logn, t);
 }
 
-// Inverse column stages (the last log2 R stages of Algorithm 7, 1/2-scaled)
-// plus the reduction to [0, q); in place on c.
-template <int R, bool HALVE>
+// Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
+// operand, column); loads the R words {c + 4096 t}, runs the first log2 R
+// stages of Algorithm 6, stores them back in place (to `dst`).
+// For polymul, operand 0 (a) goes to c and operand 1 (b) to the scratch s.
+// Each thread walks S columns (stride = the grid's thread count) and loads
+// column k+1 while it transforms column k, so that its loads are in flight
+// during the arithmetic.
+template <int R, int S>
+__global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+  const uint32_t logn = P.logn;
+  const size_t total = (size_t)P.nunits * nops * kRow;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  uint64_t nx[R];
+  auto locate = [&](size_t id, const uint64_t*& src, uint64_t*& dst, uint32_t& limb) {
+    const uint32_t col = (uint32_t)(id & (kRow - 1));
+    const size_t rest = id >> kRowLog;
+    const uint32_t op = (uint32_t)(rest % nops);
+    const uint32_t unit = (uint32_t)(rest / nops);
+    limb = unit % P.nlimbs;
+    const size_t off = ((size_t)unit << logn) + col;
+    src = (op == 0 ? P.a : P.b) + off;
+    dst = (op == 0 ? P.c : P.s) + off;
+  };
+  const uint64_t* src;
+  uint64_t* dst;
+  uint32_t limb;
+  locate(gid, src, dst, limb);
+#pragma unroll
+  for (int t = 0; t < R; t++) nx[t] = __ldcs(src + (size_t)t * kRow);
+#pragma unroll 1
+  for (int k = 0; k < S; k++) {
+    uint64_t x[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) x[t] = nx[t];
+    uint64_t* cur_dst = dst;
+    const uint32_t cur_limb = limb;
+    const size_t nid = gid + stride;
+    const bool more = (k + 1 < S) && nid < total;
+    if (more) {
+      locate(nid, src, dst, limb);
+#pragma unroll
+      for (int t = 0; t < R; t++) nx[t] = __ldcs(src + (size_t)t * kRow);
+    }
+    const LimbConst K = ld_limb(P.lc + cur_limb);
+    ct_col<R>(x, P.twf + ((size_t)cur_limb << logn), K.q, K.two_q);
+#pragma unroll
+    for (int t = 0; t < R; t++) cur_dst[(size_t)t * kRow] = x[t];
+    if (!more) break;
+    gid = nid;
+  }
+}
+
+// Inverse column stages (the last log2 R stages of Algorithm 7) plus the
+// reduction to [0, q); in place on c.  S columns per thread, software
+// pipelined as in k_col_fwd.
+template <int R, int S, bool HALVE>
 __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
   const uint32_t logn = P.logn;
-  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t col = (uint32_t)(gid & (kRow - 1));
-  const uint32_t unit = (uint32_t)(gid >> kRowLog);
-  if (unit >= P.nunits) return;
-  const uint32_t limb = unit % P.nlimbs;
-  const LimbConst K = ld_limb(P.lc + limb);
-  const TwPair* twi = P.twi + ((size_t)limb << logn);
-  uint64_t* p = P.c + ((size_t)unit << logn) + col;
-  uint64_t x[R];
+  const size_t total = (size_t)P.nunits * kRow;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  auto locate = [&](size_t id, uint64_t*& p, uint32_t& limb) {
+    const uint32_t col = (uint32_t)(id & (kRow - 1));
+    const uint32_t unit = (uint32_t)(id >> kRowLog);
+    limb = unit % P.nlimbs;
+    p = P.c + ((size_t)unit << logn) + col;
+  };
+  uint64_t* p;
+  uint32_t limb;
+  locate(gid, p, limb);
+  uint64_t nx[R];
 #pragma unroll
-  for (int t = 0; t < R; t++) x[t] = p[(size_t)t * kRow];
-  gs_col<R, HALVE>(x, twi, K);
+  for (int t = 0; t < R; t++) nx[t] = p[(size_t)t * kRow];
+#pragma unroll 1
+  for (int k = 0; k < S; k++) {
+    uint64_t x[R];
 #pragma unroll
-  for (int t = 0; t < R; t++) __stcs(p + (size_t)t * kRow, csub(x[t], K.q));
+    for (int t = 0; t < R; t++) x[t] = nx[t];
+    uint64_t* cur = p;
+    const uint32_t cur_limb = limb;
+    const size_t nid = gid + stride;
+    const bool more = (k + 1 < S) && nid < total;
+    if (more) {
+      locate(nid, p, limb);
+#pragma unroll
+      for (int t = 0; t < R; t++) nx[t] = p[(size_t)t * kRow];
+    }
+    const LimbConst K = ld_limb(P.lc + cur_limb);
+    gs_col<R, HALVE>(x, P.twi + ((size_t)cur_limb << logn), K);
+#pragma unroll
+    for (int t = 0; t < R; t++) __stcs(cur + (size_t)t * kRow, csub(x[t], K.q));
+    if (!more) break;
+    gid = nid;
+  }
 }
 
 // N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
@@ -309,22 +379,27 @@ static cudaError_t set_smem(const void* fn, int bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+// Columns per thread in the column kernels (software-pipelined loads).
+constexpr int kColsPerThread = 4;
+
 template <int R>
 static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
-  const size_t threads = (size_t)P.nunits * nops * kRow;
+  constexpr int S = (R >= 32) ? 1 : kColsPerThread;
+  const size_t threads = ((size_t)P.nunits * nops * kRow + S - 1) / S;
   const unsigned blocks = (unsigned)((threads + 255) / 256);
-  k_col_fwd<R><<<blocks, 256, 0, st>>>(P, nops);
+  k_col_fwd<R, S><<<blocks, 256, 0, st>>>(P, nops);
   return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
-  const size_t threads = (size_t)P.nunits * kRow;
+  constexpr int S = (R >= 32) ? 1 : kColsPerThread;
+  const size_t threads = ((size_t)P.nunits * kRow + S - 1) / S;
   const unsigned blocks = (unsigned)((threads + 255) / 256);
   if (P.halving)
-    k_col_inv<R, true><<<blocks, 256, 0, st>>>(P);
+    k_col_inv<R, S, true><<<blocks, 256, 0, st>>>(P);
   else
-    k_col_inv<R, false><<<blocks, 256, 0, st>>>(P);
+    k_col_inv<R, S, false><<<blocks, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
@@ -356,6 +431,13 @@ constexpr int kFused13Smem = 4 * kRowPad * 8;
 template <int MODE>
 static cudaError_t rows(const KParams& P, cudaStream_t st) {
   const unsigned blocks = P.nunits << (P.logn - kRowLog);
+  if (MODE == MODE_POLYMUL && P.row_ops == 2) {
+    if (P.halving)
+      k_rows2<true><<<blocks, 256, kRowsSmem, st>>>(P);
+    else
+      k_rows2<false><<<blocks, 256, kRowsSmem, st>>>(P);
+    return cudaGetLastError();
+  }
   if (P.halving)
     k_rows<MODE, true><<<blocks, 256, kRowsSmem, st>>>(P);
   else
@@ -386,6 +468,7 @@ template <bool H>
 static cudaError_t prepare_mode() {
   cudaError_t e;
   if ((e = set_smem((const void*)k_rows<MODE_POLYMUL, H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows2<H>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_rows<MODE_FWD, H>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_rows<MODE_INV, H>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL, H>, kFused13Smem)) != cudaSuccess) return e;

@@ -38,6 +38,34 @@ __device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __r
   }
 }
 
+// The same four stages on two operands that share the twiddles (a and b of
+// one product): each twiddle pair is loaded once and used twice.
+template <int ST>
+__device__ __forceinline__ void ct16_stage2(uint64_t (&va)[16], uint64_t (&vb)[16],
+                                            const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
+                                            uint64_t q, uint64_t two_q) {
+  constexpr int h = 8 >> ST;
+  const uint32_t base = (1u << (s0 + ST)) + (g << ST);
+#pragma unroll
+  for (int blk = 0; blk < (1 << ST); blk++) {
+    const TwPair t = ld_tw(tw + base + blk);
+#pragma unroll
+    for (int u0 = 0; u0 < h; u0++) {
+      ct_bfly(va[blk * 2 * h + u0], va[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+      ct_bfly(vb[blk * 2 * h + u0], vb[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+    }
+  }
+}
+
+__device__ __forceinline__ void ct16_2(uint64_t (&va)[16], uint64_t (&vb)[16],
+                                       const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
+                                       uint64_t q, uint64_t two_q) {
+  ct16_stage2<0>(va, vb, tw, s0, g, q, two_q);
+  ct16_stage2<1>(va, vb, tw, s0, g, q, two_q);
+  ct16_stage2<2>(va, vb, tw, s0, g, q, two_q);
+  ct16_stage2<3>(va, vb, tw, s0, g, q, two_q);
+}
+
 __device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                      uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
   ct16_stage1<0>(v, tw, s0, g, q, two_q);
@@ -286,6 +314,54 @@ __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, boo
   }
 }
 
+
+// Forward in-row stages of a and b together (shared twiddles); leaves the
+// layout-2 words of both in va, vb.
+template <bool CG = false>
+__device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16],
+                                          const uint64_t* ga, const uint64_t* gb, uint64_t* sa,
+                                          uint64_t* sb, const TwPair* __restrict__ twf,
+                                          uint32_t logn, uint32_t t, int th, uint64_t q,
+                                          uint64_t two_q) {
+#pragma unroll 1
+  for (int p = 0; p < 3; p++) {
+    const PassGeo G = pass_geo(p, th, t);
+    if (p == 0) {
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        va[u] = ld_g<CG>(ga + th + 256 * u);
+        vb[u] = ld_g<CG>(gb + th + 256 * u);
+      }
+    } else {
+      ld_smem16(va, sa, G);
+      ld_smem16(vb, sb, G);
+    }
+    ct16_2(va, vb, twf, logn - 12 + 4 * p, G.g, q, two_q);
+    if (p < 2) {
+      st_smem16(sa, G, va);
+      st_smem16(sb, G, vb);
+      __syncthreads();
+    }
+  }
+}
+
+// Polymul row task with both operands in registers at once (2 CTAs per SM).
+template <bool HALVE, bool CG>
+__device__ __forceinline__ void row_task_polymul2(const uint64_t* ga, const uint64_t* gb,
+                                                  uint64_t* gc, bool single, uint64_t* smem,
+                                                  const TwPair* __restrict__ twf,
+                                                  const TwPair* __restrict__ twi,
+                                                  const LimbConst& K, uint32_t logn, uint32_t t) {
+  const int th = threadIdx.x;
+  uint64_t* sa = smem;
+  uint64_t* sb = smem + kRowPad;
+  uint64_t va[16], vb[16];
+  rows_fwd2<CG>(va, vb, ga, gb, sa, sb, twf, logn, t, th, K.q, K.two_q);
+#pragma unroll
+  for (int u = 0; u < 16; u++)
+    va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
+  rows_inv<HALVE>(va, gc, single, sa, twi, logn, t, th, K);
+}
 
 // Polymul row task: forward in-row stages of a and b, Algorithm 4 pointwise
 // product, inverse in-row stages, for row t of `unit`.  `ga`, `gb` are the
