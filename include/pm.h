@@ -176,6 +176,40 @@ pm_status pm_polymul_host(const pm_plan *plan, const uint64_t *h_a, const uint64
                           uint64_t *h_c, uint64_t *d_a, uint64_t *d_b, uint64_t *d_c,
                           uint32_t npoly, void *stream);
 
+/* ---- Uneven batches: many products of different N and limb counts in
+ * one persistent launch (a work queue over all units).
+ * A job is npoly polynomials of one plan (its N, limbs and tables), laid
+ * out [npoly][nlimbs][N] as for pm_polymul; c may alias a or b. */
+typedef struct pm_job {
+    const pm_plan *plan;
+    const uint64_t *a;
+    const uint64_t *b;
+    uint64_t *c;
+    uint32_t npoly;
+} pm_job;
+
+/* Reusable context for uneven launches: device descriptor tables, the
+ * column-stage scratch (one N-word area per unit of N >= 2^13) and the
+ * control block, grown on demand (allocation only when growing). */
+typedef struct pm_queue pm_queue;
+pm_status pm_queue_create(pm_queue **out, int device);
+pm_status pm_queue_destroy(pm_queue *q);
+/* Pre-size for up to `units` units and `scratch_words` scratch words. */
+pm_status pm_queue_reserve(pm_queue *q, uint64_t units, uint64_t scratch_words);
+
+/* All jobs' products in one launch on `stream`.  Jobs with N >= 4096 share
+ * the launch: each CTA takes column and row tasks of any unit from a ticket
+ * counter (all column-forward tasks first, then rows, then column-inverse
+ * tasks), waiting (bounded) on per-unit counters.  Jobs with N <= 2048 run
+ * through their plan's own kernel on the same stream.  All plans must be on
+ * the queue's device and agree on PM_PLAN_HALVING.  Calls on one queue must
+ * be serialised on one stream (they share its buffers). */
+pm_status pm_polymul_uneven(pm_queue *q, const pm_job *jobs, uint32_t njobs, void *stream);
+
+/* Synchronise `stream` and report PM_ERR_TIMEOUT if an uneven launch on this
+ * queue gave up waiting for a dependency. */
+pm_status pm_queue_sync(pm_queue *q, void *stream);
+
 /* Checks 0 <= x < q_l for every coefficient of d_x [npoly][nlimbs][N];
  * returns PM_ERR_RANGE if one is out of range.  Synchronous. */
 pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t npoly,

@@ -16,7 +16,7 @@ from __future__ import annotations
 from . import capi
 from .capi import PMError, pm_find_params  # noqa: F401
 
-__all__ = ["Plan", "find_params", "PMError", "capi"]
+__all__ = ["Plan", "Queue", "find_params", "PMError", "capi"]
 
 
 def find_params(n: int, nlimbs: int = 1, qbits: int = 60):
@@ -147,3 +147,38 @@ class Plan:
 
     def sync(self, stream=None) -> None:
         capi.pm_plan_sync(self.handle, _stream_handle(stream))
+
+
+class Queue:
+    """Reusable context for uneven batches (pm_polymul_uneven)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self._h = capi.pm_queue_create(device)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            capi.pm_queue_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, units: int, scratch_words: int) -> None:
+        capi.pm_queue_reserve(self._h, units, scratch_words)
+
+    def polymul_uneven(self, jobs, stream=None) -> None:
+        """jobs: list of (Plan, a, b, c) with CUDA tensors shaped for the plan."""
+        raw = []
+        for plan, a, b, c in jobs:
+            npoly = plan._npoly(a)
+            if plan._npoly(b) != npoly or plan._npoly(c) != npoly:
+                raise ValueError("a, b, c differ in size")
+            raw.append((plan.handle, a.data_ptr(), b.data_ptr(), c.data_ptr(), npoly))
+        capi.pm_polymul_uneven(self._h, raw, _stream_handle(stream))
+
+    def sync(self, stream=None) -> None:
+        capi.pm_queue_sync(self._h, _stream_handle(stream))

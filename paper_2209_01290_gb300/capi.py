@@ -49,6 +49,11 @@ SIGNATURES = {
     "pm_version": (ctypes.c_char_p, []),
     "pm_measure_peaks": (_i32, [_i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double)]),
+    "pm_queue_create": (_i32, [ctypes.POINTER(_vp), _i32]),
+    "pm_queue_destroy": (_i32, [_vp]),
+    "pm_queue_reserve": (_i32, [_vp, _u64, _u64]),
+    "pm_polymul_uneven": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_queue_sync": (_i32, [_vp, _vp]),
 }
 
 _lib = None
@@ -232,6 +237,35 @@ def pm_measure_peaks(device: int = 0):
     st = load().pm_measure_peaks(device, ctypes.byref(m), ctypes.byref(i))
     check(st, "pm_measure_peaks")
     return m.value, i.value
+
+
+class PmJob(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("npoly", ctypes.c_uint32)]
+
+
+def pm_queue_create(device: int = 0) -> int:
+    out = ctypes.c_void_p()
+    _call("pm_queue_create", ctypes.byref(out), device)
+    return out.value
+
+
+def pm_queue_destroy(q: int) -> None:
+    _call("pm_queue_destroy", q)
+
+
+def pm_queue_reserve(q: int, units: int, scratch_words: int) -> None:
+    _call("pm_queue_reserve", q, units, scratch_words)
+
+
+def pm_polymul_uneven(q: int, jobs, stream: int = 0) -> None:
+    """jobs: sequence of (plan handle, d_a, d_b, d_c, npoly)."""
+    arr = (PmJob * max(1, len(jobs)))(*[PmJob(*j) for j in jobs])
+    _call("pm_polymul_uneven", q, arr, len(jobs), stream)
+
+
+def pm_queue_sync(q: int, stream: int = 0) -> None:
+    _call("pm_queue_sync", q, stream)
 
 
 def pm_version() -> str:

@@ -693,4 +693,247 @@ pm_status pm_plan_get_tuning(const pm_plan* plan, pm_tuning* t) {
   return ok();
 }
 
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- uneven batch
+
+struct pm_queue {
+  int device = 0;
+  int num_sms = 0;
+  std::mutex mu;
+  pm::UnitDesc* d_units = nullptr;
+  uint32_t* d_pre = nullptr;  // [3][cap]
+  uint32_t* d_ctl = nullptr;  // [4 + 2 cap]
+  size_t cap = 0;
+  uint64_t* d_scratch = nullptr;
+  size_t scratch_words = 0;
+  pm::UnitDesc* h_units = nullptr;  // pinned staging
+  uint32_t* h_pre = nullptr;
+  size_t h_cap = 0;
+  cudaEvent_t staged = nullptr;  // the last upload from the staging buffers
+  bool staged_used = false;
+};
+
+namespace {
+
+void destroy_queue(pm_queue* q) {
+  if (!q) return;
+  DeviceGuard g(q->device);
+  cudaFree(q->d_units);
+  cudaFree(q->d_pre);
+  cudaFree(q->d_ctl);
+  cudaFree(q->d_scratch);
+  cudaFreeHost(q->h_units);
+  cudaFreeHost(q->h_pre);
+  if (q->staged) cudaEventDestroy(q->staged);
+  delete q;
+}
+
+pm_status queue_reserve(pm_queue* q, size_t units, size_t scratch_words) {
+  cudaError_t e;
+  if (units > q->cap) {
+    if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
+      return cuda_fail(e, "queue staging");
+    cudaFree(q->d_units);
+    cudaFree(q->d_pre);
+    cudaFree(q->d_ctl);
+    cudaFreeHost(q->h_units);
+    cudaFreeHost(q->h_pre);
+    q->d_units = nullptr;
+    q->d_pre = q->d_ctl = nullptr;
+    q->h_units = nullptr;
+    q->h_pre = nullptr;
+    q->cap = q->h_cap = 0;
+    const size_t cap = units < 256 ? 256 : units;
+    if ((e = cudaMalloc(&q->d_units, cap * sizeof(pm::UnitDesc))) != cudaSuccess ||
+        (e = cudaMalloc(&q->d_pre, 3 * cap * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&q->d_ctl, (4 + 2 * cap) * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMallocHost(&q->h_units, cap * sizeof(pm::UnitDesc))) != cudaSuccess ||
+        (e = cudaMallocHost(&q->h_pre, 3 * cap * sizeof(uint32_t))) != cudaSuccess)
+      return cuda_fail(e, "queue buffers");
+    if ((e = cudaMemset(q->d_ctl, 0, (4 + 2 * cap) * sizeof(uint32_t))) != cudaSuccess)
+      return cuda_fail(e, "queue ctl");
+    q->cap = q->h_cap = cap;
+    q->staged_used = false;
+  }
+  if (scratch_words > q->scratch_words) {
+    cudaFree(q->d_scratch);
+    q->d_scratch = nullptr;
+    q->scratch_words = 0;
+    if ((e = cudaMalloc(&q->d_scratch, scratch_words * 8)) != cudaSuccess)
+      return cuda_fail(e, "queue scratch");
+    q->scratch_words = scratch_words;
+  }
+  return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_queue_create(pm_queue** out, int device) {
+  if (!out) return fail(PM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(PM_ERR_ARG, "device %d not present", device);
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_queue* q = new (std::nothrow) pm_queue();
+  if (!q) return fail(PM_ERR_OOM, "host allocation failed");
+  q->device = device;
+  if ((e = cudaDeviceGetAttribute(&q->num_sms, cudaDevAttrMultiProcessorCount, device)) !=
+          cudaSuccess ||
+      (e = prepare_device(device)) != cudaSuccess || (e = pm::persist_prepare()) != cudaSuccess ||
+      (e = pm::uneven_prepare()) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&q->staged, cudaEventDisableTiming)) != cudaSuccess) {
+    destroy_queue(q);
+    return cuda_fail(e, "queue setup");
+  }
+  *out = q;
+  return ok();
+}
+
+pm_status pm_queue_destroy(pm_queue* q) {
+  destroy_queue(q);
+  return ok();
+}
+
+pm_status pm_queue_reserve(pm_queue* q, uint64_t units, uint64_t scratch_words) {
+  if (!q) return fail(PM_ERR_ARG, "queue is NULL");
+  DeviceGuard g(q->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  std::lock_guard<std::mutex> lk(q->mu);
+  pm_status s = queue_reserve(q, units, scratch_words);
+  return s == PM_OK ? ok() : s;
+}
+
+pm_status pm_polymul_uneven(pm_queue* q, const pm_job* jobs, uint32_t njobs, void* stream) {
+  if (!q) return fail(PM_ERR_ARG, "queue is NULL");
+  if (njobs == 0) return ok();
+  if (!jobs) return fail(PM_ERR_ARG, "jobs is NULL");
+  // validate and size
+  uint64_t units = 0, scratch = 0;
+  int halving = -1;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
+    if (J.plan->device != q->device)
+      return fail(PM_ERR_ARG, "job %u: plan on device %d, queue on %d", j, J.plan->device, q->device);
+    if (J.npoly == 0) return fail(PM_ERR_ARG, "job %u: npoly is 0", j);
+    if (!J.a || !J.b || !J.c || !aligned16(J.a) || !aligned16(J.b) || !aligned16(J.c))
+      return fail(PM_ERR_ARG, "job %u: NULL or misaligned pointer", j);
+    if (J.plan->logn < 12) continue;  // run through the plan's own path below
+    const int h = (J.plan->flags & PM_PLAN_HALVING) ? 1 : 0;
+    if (halving >= 0 && h != halving)
+      return fail(PM_ERR_ARG, "jobs mix PM_PLAN_HALVING and default plans");
+    halving = h;
+    const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
+    units += u;
+    if (J.plan->logn > 12 && J.a != J.b) scratch += u << J.plan->logn;
+  }
+  if (units > 0x3fffffffull) return fail(PM_ERR_ARG, "too many units (%llu)", (unsigned long long)units);
+  DeviceGuard g(q->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  std::lock_guard<std::mutex> lk(q->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  // small-N jobs: their plan's own path, on the same stream
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    if (J.plan->logn >= 12) continue;
+    pm_plan* p = const_cast<pm_plan*>(J.plan);
+    std::lock_guard<std::mutex> lp(p->mu);
+    pm_status s2 = polymul_impl(p, J.a, J.b, J.c, J.npoly, st);
+    if (s2 != PM_OK) return s2;
+  }
+  if (units == 0) return ok();
+  pm_status s = queue_reserve(q, units, scratch ? scratch : 1);
+  if (s != PM_OK) return s;
+  if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
+    return cuda_fail(e, "queue staging");
+  // unit descriptors and section prefix counts
+  uint32_t* pf = q->h_pre;
+  uint32_t* pw = q->h_pre + units;
+  uint32_t* pi = q->h_pre + 2 * units;
+  uint32_t tf = 0, tw = 0, ti = 0;
+  uint64_t soff = 0;
+  size_t u = 0;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    const pm_plan* p = J.plan;
+    if (p->logn < 12) continue;
+    const uint64_t n = (uint64_t)1 << p->logn;
+    const bool split = p->logn > 12;
+    const bool square = J.a == J.b;
+    for (uint32_t k = 0; k < J.npoly * p->nlimbs; ++k, ++u) {
+      pm::UnitDesc& D = q->h_units[u];
+      const uint32_t limb = k % p->nlimbs;
+      D.a = J.a + k * n;
+      D.b = J.b + k * n;
+      D.c = J.c + k * n;
+      if (split && !square) {
+        D.s = q->d_scratch + soff;
+        soff += n;
+        if (J.c == J.b) std::swap(D.a, D.b);  // b's image stays in place in c
+      } else {
+        D.s = D.c;
+      }
+      D.twf = p->d_twf + ((size_t)limb << p->logn);
+      D.twi = p->d_twi + ((size_t)limb << p->logn);
+      D.lc = p->d_lc + limb;
+      D.logn = p->logn;
+      D.pad = 0;
+      pf[u] = tf;
+      pw[u] = tw;
+      pi[u] = ti;
+      tf += split ? (square ? 1u : 2u) * 16u : 0u;
+      tw += (uint32_t)(n >> 12);
+      ti += split ? 16u : 0u;
+    }
+  }
+  // the three prefix arrays are uploaded contiguously, in the order f, w, i
+  if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(q->d_pre, q->h_pre, 3 * units * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
+    return cuda_fail(e, "queue upload");
+  q->staged_used = true;
+  pm::UnevenArgs A{};
+  A.units = q->d_units;
+  A.pre_f = q->d_pre;
+  A.pre_w = q->d_pre + units;
+  A.pre_i = q->d_pre + 2 * units;
+  A.ctl = q->d_ctl;
+  A.nunits = (uint32_t)units;
+  A.tf = tf;
+  A.tw = tw;
+  A.ti = ti;
+  if ((e = pm::launch_uneven(A, halving == 1, q->num_sms * 3, st)) != cudaSuccess)
+    return cuda_fail(e, "uneven launch");
+  return ok();
+}
+
+pm_status pm_queue_sync(pm_queue* q, void* stream) {
+  if (!q) return fail(PM_ERR_ARG, "queue is NULL");
+  DeviceGuard g(q->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  std::lock_guard<std::mutex> lk(q->mu);
+  if (q->d_ctl) {
+    uint32_t flag = 0;
+    if ((e = cudaMemcpy(&flag, q->d_ctl + 1, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "read status");
+    if (flag) {
+      cudaMemset(q->d_ctl + 1, 0, 4);
+      return fail(PM_ERR_TIMEOUT, "the uneven launch gave up waiting for a dependency");
+    }
+  }
+  return ok();
+}
+
 }  // extern "C"

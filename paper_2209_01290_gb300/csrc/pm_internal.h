@@ -43,6 +43,32 @@ struct PersistArgs {
   uint32_t withheld;  // fault injection: row tasks wait for this many extra signals (0)
 };
 
+// Uneven batch (pm_persist.cu): one descriptor per unit.
+struct alignas(64) UnitDesc {
+  const uint64_t* a;     // operand rows of this unit (device)
+  const uint64_t* b;     // == a for a square
+  uint64_t* c;           // output; also receives a's column-stage image
+  uint64_t* s;           // scratch N words for b's image (== c for a square)
+  const TwPair* twf;     // the unit's limb tables (its plan)
+  const TwPair* twi;
+  const LimbConst* lc;
+  uint32_t logn;
+  uint32_t pad;
+};
+
+struct UnevenArgs {
+  const UnitDesc* units;
+  const uint32_t* pre_f;  // [nunits] exclusive prefix counts of column-forward tasks
+  const uint32_t* pre_w;  // ... of row tasks
+  const uint32_t* pre_i;  // ... of column-inverse tasks
+  uint32_t* ctl;          // [0] ticket, [1] error flag, [4 + 2u] per-unit counters
+  uint32_t nunits;
+  uint32_t tf, tw, ti;    // tickets per section
+};
+
+cudaError_t uneven_prepare();
+cudaError_t launch_uneven(const UnevenArgs& A, bool halving, int grid, cudaStream_t st);
+
 cudaError_t persist_prepare();
 size_t persist_ctl_words(uint32_t nunits);
 cudaError_t launch_polymul_persistent(const KParams& P, uint32_t* ctl, int grid, uint32_t lagF,

@@ -318,4 +318,127 @@ cudaError_t launch_polymul_persistent(const KParams& P0, uint32_t* ctl, int grid
   return cudaErrorInvalidValue;
 }
 
+
+// --------------------------------------------------------------------------
+// Uneven batch: products of different N and limb counts in one launch.
+//
+// Every (job, polynomial, limb) is a unit with its own descriptor (pointers,
+// plan tables, log2 N).  The tickets are laid out in three sections -- all
+// column-forward tasks, then all row tasks, then all column-inverse tasks,
+// each ordered by unit -- and decoded with a binary search over per-unit
+// prefix counts.  Dependencies and bounded waits are the same as above.
+// N = 4096 units have only a row task; N <= 2048 is not handled here (the
+// host routes such jobs to the per-plan path).
+
+namespace {
+
+__device__ __forceinline__ uint32_t find_unit(const uint32_t* __restrict__ pre, uint32_t n,
+                                              uint32_t x) {
+  // largest u with pre[u] <= x, pre[0] = 0, pre non-decreasing, n >= 1
+  uint32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool HALVE>
+__device__ void run_uneven_task(const UnevenArgs& A, uint32_t ticket, uint64_t* smem) {
+  uint32_t* done = A.ctl + 4;
+  int* err = reinterpret_cast<int*>(A.ctl + 1);
+  const uint32_t U = A.nunits;
+  uint32_t section, base;
+  const uint32_t* pre;
+  if (ticket < A.tf) {
+    section = 0; base = 0; pre = A.pre_f;
+  } else if (ticket < A.tf + A.tw) {
+    section = 1; base = A.tf; pre = A.pre_w;
+  } else {
+    section = 2; base = A.tf + A.tw; pre = A.pre_i;
+  }
+  __shared__ uint32_t s_unit;
+  if (threadIdx.x == 0) s_unit = find_unit(pre, U, ticket - base);
+  __syncthreads();
+  const uint32_t unit = s_unit;
+  __syncthreads();
+  const UnitDesc D = A.units[unit];
+  const uint32_t r = ticket - base - __ldg(pre + unit);
+  const uint32_t logn = D.logn;
+  const uint32_t R = 1u << (logn - kRowLog);
+  const LimbConst K = ld_limb(D.lc);
+  if (section == 0) {
+    const uint32_t op = r / (kRow / kTaskCols), cs = r % (kRow / kTaskCols);
+    const size_t off = cs * kTaskCols + threadIdx.x;
+    const uint64_t* src = (op == 0 ? D.a : D.b) + off;
+    uint64_t* dst = (op == 0 ? D.c : D.s) + off;
+    switch (R) {
+      case 2: colf_regs<2>(src, dst, D.twf, K); break;
+      case 4: colf_regs<4>(src, dst, D.twf, K); break;
+      case 8: colf_regs<8>(src, dst, D.twf, K); break;
+      case 16: colf_regs<16>(src, dst, D.twf, K); break;
+      default: colf_32(src, dst, smem, D.twf, K); break;
+    }
+    cta_signal(done + 2 * unit);
+  } else if (section == 1) {
+    const uint32_t nf = (logn > kRowLog) ? ((D.a == D.b ? 1u : 2u) * (kRow / kTaskCols)) : 0u;
+    if (nf) cta_wait(done + 2 * unit, nf, err);
+    const size_t off = (size_t)r * kRow;
+    const bool single = (logn == kRowLog);
+    row_task_polymul<HALVE, true>((single ? D.a : D.c) + off, (single ? D.b : D.s) + off,
+                                  D.c + off, single, smem, D.twf, D.twi, K, logn, r);
+    if (!single) cta_signal(done + 2 * unit + 1);
+  } else {
+    cta_wait(done + 2 * unit + 1, R, err);
+    uint64_t* p = D.c + r * kTaskCols + threadIdx.x;
+    switch (R) {
+      case 2: coli_regs<2, HALVE>(p, D.twi, K); break;
+      case 4: coli_regs<4, HALVE>(p, D.twi, K); break;
+      case 8: coli_regs<8, HALVE>(p, D.twi, K); break;
+      case 16: coli_regs<16, HALVE>(p, D.twi, K); break;
+      default: coli_32<HALVE>(p, smem, D.twi, K); break;
+    }
+  }
+}
+
+}  // namespace
+
+template <bool HALVE>
+__global__ void __launch_bounds__(256, 3) k_uneven(UnevenArgs A) {
+  extern __shared__ __align__(16) uint64_t smem[];
+  __shared__ uint32_t s_ticket;
+  const uint32_t total = A.tf + A.tw + A.ti;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(A.ctl, 1u);
+    __syncthreads();
+    const uint32_t ticket = s_ticket;
+    __syncthreads();
+    if (ticket >= total) break;
+    run_uneven_task<HALVE>(A, ticket, smem);
+    __syncthreads();
+  }
+}
+
+cudaError_t uneven_prepare() {
+  cudaError_t e = cudaFuncSetAttribute((const void*)k_uneven<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute((const void*)k_uneven<true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+}
+
+cudaError_t launch_uneven(const UnevenArgs& A, bool halving, int grid, cudaStream_t st) {
+  if (A.nunits == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(A.ctl, 0, (4 + 2 * (size_t)A.nunits) * 4, st);
+  if (e != cudaSuccess) return e;
+  if (halving)
+    k_uneven<true><<<grid, 256, kPersistSmem, st>>>(A);
+  else
+    k_uneven<false><<<grid, 256, kPersistSmem, st>>>(A);
+  return cudaGetLastError();
+}
+
 }  // namespace pm

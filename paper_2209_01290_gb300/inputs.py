@@ -39,6 +39,20 @@ def uniform_limbs(seed: int, qs, npoly: int, n: int) -> np.ndarray:
     return out
 
 
+def uniform_limbs_torch(seed: int, qs, npoly: int, n: int, device="cuda"):
+    """Device-side version of uniform_limbs for large batches: int64 tensor
+    [npoly][L][n], limb l uniform in [0, qs[l]) (torch's seeded generator;
+    a different stream of numbers than the numpy generator)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((npoly, len(qs), n), dtype=torch.int64, device=device)
+    for l, q in enumerate(qs):
+        out[:, l, :] = torch.randint(0, int(q), (npoly, n), generator=g, device=device,
+                                     dtype=torch.int64)
+    return out
+
+
 def operand_pair(seed: int, qs, npoly: int, n: int):
     """(a, b), each [npoly][L][n], independent uniform draws."""
     a = uniform_limbs(seed, qs, npoly, n)
