@@ -56,6 +56,7 @@ def test_withheld_signal_times_out_then_recovers(oracle):
     import time
     from paper_2209_01290_gb300 import capi
     plan, qs, psis, a, b = _setup(14, 1, 2, 12000)
+    capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT)
     want = oracle_polymul_batch(oracle, a, b, qs, psis)
     da, db = to_dev(a), to_dev(b)
     capi.pm_plan_inject_fault(plan.handle, capi.PM_FAULT_WITHHOLD_SIGNAL)
