@@ -334,6 +334,161 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------------ workloads
+# Secondary measurements for the other configurations (one JSON line each);
+# the default workload above is the headline.
+
+def _flush_l2(buf):
+    buf.add_(1)  # writes 256 MiB: larger than the 129 MB L2
+
+
+def _time_each(fn, reps, stream, flush=None):
+    import torch
+    out = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def run_workload(args):
+    import torch
+    from paper_2209_01290_gb300 import Plan, Queue, capi, inputs
+    dev = torch.cuda.current_device()
+    st = torch.cuda.Stream(device=dev)
+    flushbuf = torch.zeros(32 << 20, dtype=torch.int64, device=dev)
+    lines = []
+    if args.workload == "c1":
+        n = 1 << 12
+        qs, psis = capi.pm_find_params(12, 1, 60)
+        plan = Plan(n, qs, psis)
+        a, b = inputs.operand_pair(inputs.seed_for(0), qs, 1, n)
+        da = torch.from_numpy(a.view(np.int64)).to(dev)
+        db = torch.from_numpy(b.view(np.int64)).to(dev)
+        dc = torch.empty_like(da)
+        g = plan.graph_polymul(da, db, dc)
+        for _ in range(args.warmup):
+            g.launch(st)
+        st.synchronize()
+        lat = _time_each(lambda: g.launch(st), max(args.steps, 50), st)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(1000):
+            g.launch(st)
+        e1.record(st)
+        st.synchronize()
+        lines.append({"workload": "c1: one N=2^12 product, graph-launched", "metric": "latency",
+                      "p50_us": 1e3 * float(np.median(lat)), "p99_us": 1e3 * float(np.percentile(lat, 99)),
+                      "back_to_back_polymuls_per_s": 1000 / (e0.elapsed_time(e1) * 1e-3)})
+    elif args.workload == "c2sweep":
+        for log2n in range(13, 18):
+            n = 1 << log2n
+            qs, psis = capi.pm_find_params(log2n, 1, 60)
+            plan = Plan(n, qs, psis)
+            a, b = inputs.operand_pair(inputs.seed_for(1) + log2n, qs, 1, n)
+            da = torch.from_numpy(a.view(np.int64)).to(dev)
+            db = torch.from_numpy(b.view(np.int64)).to(dev)
+            dc = torch.empty_like(da)
+            plan.reserve(1, stream=st)
+            res = {"workload": f"c2: N=2^{log2n}, single product", "N": n}
+            for name, fn in [("polymul", lambda: plan.polymul(da, db, out=dc, stream=st)),
+                             ("ntt_fwd", lambda: plan.ntt_fwd_(dc, stream=st)),
+                             ("ntt_inv", lambda: plan.ntt_inv_(dc, stream=st))]:
+                for _ in range(args.warmup):
+                    fn()
+                t = _time_each(fn, 30, st, flush=lambda: _flush_l2(flushbuf))
+                res[name + "_us_median"] = 1e3 * float(np.median(t))
+            # batched throughput (about 1 GiB of operands)
+            P = max(1, (1 << 26) // n)
+            A = inputs.uniform_limbs_torch(log2n, qs, P, n, device=dev)
+            B = inputs.uniform_limbs_torch(log2n + 100, qs, P, n, device=dev)
+            C = torch.empty_like(A)
+            plan.reserve(P, stream=st)
+            for _ in range(args.warmup):
+                plan.polymul(A, B, out=C, stream=st)
+            t = _time_each(lambda: plan.polymul(A, B, out=C, stream=st), 10, st)
+            res["batched_products"] = P
+            res["batched_polymuls_per_s"] = P / (float(np.median(t)) * 1e-3)
+            lines.append(res)
+    elif args.workload == "c3":
+        log2n, L = 16, 32
+        n = 1 << log2n
+        qs, psis = capi.pm_find_params(log2n, L, 60)
+        plan = Plan(n, qs, psis)
+        A = inputs.uniform_limbs_torch(inputs.seed_for(2), qs, 1, n, device=dev)
+        B = inputs.uniform_limbs_torch(inputs.seed_for(2) + 1, qs, 1, n, device=dev)
+        C = torch.empty_like(A)
+        res = {"workload": "c3: N=2^16, 32 RNS limbs (32 distinct 60-bit primes), one product per limb",
+               "l2": "256 MiB written between iterations"}
+        for vname, variant in [("split", capi.PM_VARIANT_SPLIT), ("persistent", capi.PM_VARIANT_PERSISTENT)]:
+            capi.pm_plan_tune(plan.handle, variant, 3, 2, 16)
+            g = plan.graph_polymul(A, B, C)
+            for _ in range(args.warmup):
+                g.launch(st)
+            t = _time_each(lambda: g.launch(st), 30, st, flush=lambda: _flush_l2(flushbuf))
+            res[f"graph_{vname}_us_median"] = 1e3 * float(np.median(t))
+            g.close()
+        # 32 plain launches: one single-limb plan and call per limb
+        single = [Plan(n, [qs[l]], [psis[l]]) for l in range(L)]
+        for p1 in single:
+            p1.reserve(1, stream=st)
+        def per_limb():
+            for l in range(L):
+                single[l].polymul(A[:, l], B[:, l], out=C[:, l], stream=st)
+        for _ in range(args.warmup):
+            per_limb()
+        t = _time_each(per_limb, 30, st, flush=lambda: _flush_l2(flushbuf))
+        res["per_limb_launches_us_median"] = 1e3 * float(np.median(t))
+        best = min(v for k, v in res.items() if k.startswith("graph_"))
+        res["batched_speedup_vs_per_limb"] = res["per_limb_launches_us_median"] / best
+        res["polymuls_per_s_batched"] = L / (best * 1e-6)
+        lines.append(res)
+    elif args.workload == "c4":
+        shapes = inputs.uneven_shapes(inputs.seed_for(3), njobs=512)
+        plans, jobs = {}, []
+        units = 0
+        for j, sh in enumerate(shapes):
+            key = (sh.log2n, sh.nlimbs)
+            if key not in plans:
+                q_, p_ = capi.pm_find_params(sh.log2n, sh.nlimbs, 60)
+                plans[key] = Plan(1 << sh.log2n, q_, p_)
+            plan = plans[key]
+            a = inputs.uniform_limbs_torch(inputs.seed_for(3) + 2 * j, plan.qs, 1, 1 << sh.log2n, device=dev)
+            b = inputs.uniform_limbs_torch(inputs.seed_for(3) + 2 * j + 1, plan.qs, 1, 1 << sh.log2n, device=dev)
+            jobs.append((plan, a, b, torch.empty_like(a)))
+            units += sh.nlimbs
+        q = Queue(dev)
+        for _ in range(args.warmup):
+            q.polymul_uneven(jobs, stream=st)
+        q.sync(st)
+        t1 = _time_each(lambda: q.polymul_uneven(jobs, stream=st), 10, st)
+        for plan in plans.values():
+            plan.reserve(1, stream=st)
+        def per_job():
+            for plan, a, b, c in jobs:
+                plan.polymul(a, b, out=c, stream=st)
+        for _ in range(args.warmup):
+            per_job()
+        t2 = _time_each(per_job, 10, st)
+        mm = sum(mulmods_per_polymul(sh.log2n) * sh.nlimbs for sh in shapes)
+        lines.append({"workload": "c4: 512 uneven jobs, N in 2^12..2^17, 1..48 limbs",
+                      "units": units, "operand_gib": sum((1 << sh.log2n) * sh.nlimbs for sh in shapes) * 8 / 2**30,
+                      "one_launch_ms_median": float(np.median(t1)),
+                      "per_job_launches_ms_median": float(np.median(t2)),
+                      "one_launch_speedup": float(np.median(t2)) / float(np.median(t1)),
+                      "one_launch_polymuls_per_s": units / (float(np.median(t1)) * 1e-3),
+                      "one_launch_tmulmod_per_s": mm / (float(np.median(t1)) * 1e-3) / 1e12})
+    for line in lines:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,6 +501,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "c1", "c2sweep", "c3", "c4"])
     ap.add_argument("--ctas-per-sm", type=int, default=3)
     ap.add_argument("--lag-fwd", type=int, default=8)
     ap.add_argument("--lag-inv", type=int, default=16)
@@ -354,6 +510,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "headline":
+        return run_workload(args)
     return run_gpu(args)
 
 

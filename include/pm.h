@@ -176,6 +176,17 @@ pm_status pm_polymul_host(const pm_plan *plan, const uint64_t *h_a, const uint64
                           uint64_t *h_c, uint64_t *d_a, uint64_t *d_b, uint64_t *d_c,
                           uint32_t npoly, void *stream);
 
+/* ---- CUDA graphs: pm_polymul for fixed buffers, captured once and
+ * replayed with one cudaGraphLaunch.  The graph owns its own scratch and
+ * control block (allocated at creation), so replays allocate nothing.
+ * Replays of one graph must not overlap on the device (they share its
+ * scratch); the captured launch choice is the plan's tuning at creation. */
+typedef struct pm_graph pm_graph;
+pm_status pm_graph_create_polymul(pm_graph **out, const pm_plan *plan, const uint64_t *d_a,
+                                  const uint64_t *d_b, uint64_t *d_c, uint32_t npoly);
+pm_status pm_graph_launch(pm_graph *g, void *stream);
+pm_status pm_graph_destroy(pm_graph *g);
+
 /* ---- Uneven batches: many products of different N and limb counts in
  * one persistent launch (a work queue over all units).
  * A job is npoly polynomials of one plan (its N, limbs and tables), laid

@@ -141,12 +141,42 @@ class Plan:
     def reserve(self, npoly: int, stream=None) -> None:
         capi.pm_plan_reserve(self.handle, npoly, _stream_handle(stream))
 
+    def graph_polymul(self, a, b, c) -> "Graph":
+        """Capture c = a * b into a CUDA graph (replay with Graph.launch)."""
+        npoly = self._npoly(a)
+        if self._npoly(b) != npoly or self._npoly(c) != npoly:
+            raise ValueError("a, b, c differ in size")
+        return Graph(capi.pm_graph_create_polymul(self.handle, a.data_ptr(), b.data_ptr(),
+                                                  c.data_ptr(), npoly), self.device)
+
     def check_reduced(self, x, stream=None) -> bool:
         npoly = self._npoly(x)
         return capi.pm_check_reduced(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
 
     def sync(self, stream=None) -> None:
         capi.pm_plan_sync(self.handle, _stream_handle(stream))
+
+
+class Graph:
+    """A captured polymul (pm_graph_create_polymul)."""
+
+    def __init__(self, handle: int, device: int):
+        self._h = handle
+        self.device = device
+
+    def launch(self, stream=None) -> None:
+        capi.pm_graph_launch(self._h, _stream_handle(stream))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            capi.pm_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Queue:

@@ -49,6 +49,9 @@ SIGNATURES = {
     "pm_version": (ctypes.c_char_p, []),
     "pm_measure_peaks": (_i32, [_i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double)]),
+    "pm_graph_create_polymul": (_i32, [ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _u32]),
+    "pm_graph_launch": (_i32, [_vp, _vp]),
+    "pm_graph_destroy": (_i32, [_vp]),
     "pm_queue_create": (_i32, [ctypes.POINTER(_vp), _i32]),
     "pm_queue_destroy": (_i32, [_vp]),
     "pm_queue_reserve": (_i32, [_vp, _u64, _u64]),
@@ -237,6 +240,20 @@ def pm_measure_peaks(device: int = 0):
     st = load().pm_measure_peaks(device, ctypes.byref(m), ctypes.byref(i))
     check(st, "pm_measure_peaks")
     return m.value, i.value
+
+
+def pm_graph_create_polymul(plan: int, d_a: int, d_b: int, d_c: int, npoly: int) -> int:
+    out = ctypes.c_void_p()
+    _call("pm_graph_create_polymul", ctypes.byref(out), plan, d_a, d_b, d_c, npoly)
+    return out.value
+
+
+def pm_graph_launch(g: int, stream: int = 0) -> None:
+    _call("pm_graph_launch", g, stream)
+
+
+def pm_graph_destroy(g: int) -> None:
+    _call("pm_graph_destroy", g)
 
 
 class PmJob(ctypes.Structure):

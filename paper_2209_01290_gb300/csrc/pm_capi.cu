@@ -937,3 +937,99 @@ pm_status pm_queue_sync(pm_queue* q, void* stream) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- graphs
+
+struct pm_graph {
+  int device = 0;
+  uint64_t* scratch = nullptr;
+  uint32_t* ctl = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+void destroy_graph(pm_graph* g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  cudaFree(g->scratch);
+  cudaFree(g->ctl);
+  delete g;
+}
+}  // namespace
+
+extern "C" {
+
+pm_status pm_graph_create_polymul(pm_graph** out, const pm_plan* plan, const uint64_t* d_a,
+                                  const uint64_t* d_b, uint64_t* d_c, uint32_t npoly) {
+  if (!out) return fail(PM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard dg(plan->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  pm_graph* g = new (std::nothrow) pm_graph();
+  if (!g) return fail(PM_ERR_OOM, "host allocation failed");
+  g->device = plan->device;
+  pm::KParams P = base_params(plan, npoly);
+  P.a = d_a;
+  P.b = d_b;
+  P.c = d_c;
+  const bool persistent = use_persistent(plan);
+  cudaError_t e = cudaSuccess;
+  if (pm::polymul_needs_scratch(plan->logn) || (persistent && plan->logn >= 13)) {
+    if ((e = cudaMalloc(&g->scratch, (size_t)P.nunits << plan->logn << 3)) != cudaSuccess) {
+      destroy_graph(g);
+      return cuda_fail(e, "cudaMalloc(graph scratch)");
+    }
+    P.s = g->scratch;
+  }
+  if (persistent &&
+      (e = cudaMalloc(&g->ctl, pm::persist_ctl_words(P.nunits) * 4)) != cudaSuccess) {
+    destroy_graph(g);
+    return cuda_fail(e, "cudaMalloc(graph ctl)");
+  }
+  cudaStream_t cap = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    destroy_graph(g);
+    return cuda_fail(e, "capture stream");
+  }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = persistent ? pm::launch_polymul_persistent(
+                                      P, g->ctl, plan->num_sms * (int)plan->tune.ctas_per_sm,
+                                      plan->tune.lag_fwd, plan->tune.lag_inv, cap)
+                                : pm::launch_polymul(P, cap);
+    e = cudaStreamEndCapture(cap, &g->graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    destroy_graph(g);
+    return cuda_fail(e, "graph capture");
+  }
+  *out = g;
+  return ok();
+}
+
+pm_status pm_graph_launch(pm_graph* g, void* stream) {
+  if (!g) return fail(PM_ERR_ARG, "graph is NULL");
+  DeviceGuard dg(g->device);
+  if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return ok();
+}
+
+pm_status pm_graph_destroy(pm_graph* g) {
+  destroy_graph(g);
+  return ok();
+}
+
+}  // extern "C"

@@ -69,3 +69,24 @@ def test_withheld_signal_times_out_then_recovers(oracle):
     got = to_host(plan.polymul(da, db))
     plan.sync()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("variant", [0, 1], ids=["split", "persistent"])
+@pytest.mark.parametrize("log2n", [12, 13, 16, 17])
+def test_graph_replay(oracle, log2n, variant):
+    """A captured polymul replays bit-exactly, also after the inputs change."""
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis, a, b = _setup(log2n, 2, 2, 13000 + log2n)
+    capi.pm_plan_tune(plan.handle, variant)
+    da, db = to_dev(a), to_dev(b)
+    dc = da.new_empty(da.shape)
+    g = plan.graph_polymul(da, db, dc)
+    for rep in range(2):
+        if rep:
+            a, b = operands(13100 + log2n, qs, 2, 1 << log2n)
+            da.copy_(to_dev(a))
+            db.copy_(to_dev(b))
+        g.launch()
+        plan.sync()
+        assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis)), rep
+    g.close()
