@@ -379,27 +379,42 @@ static cudaError_t set_smem(const void* fn, int bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// Columns per thread in the column kernels (software-pipelined loads).
+// Columns per thread in the column kernels (software-pipelined loads).  Only
+// batches of at least kPipeMinCols columns use it; small batches keep one
+// column per thread so that they spread over as many SMs as possible.
 constexpr int kColsPerThread = 4;
+constexpr size_t kPipeMinCols = (size_t)1 << 20;
 
 template <int R>
 static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
-  constexpr int S = (R >= 32) ? 1 : kColsPerThread;
-  const size_t threads = ((size_t)P.nunits * nops * kRow + S - 1) / S;
-  const unsigned blocks = (unsigned)((threads + 255) / 256);
-  k_col_fwd<R, S><<<blocks, 256, 0, st>>>(P, nops);
+  const size_t cols = (size_t)P.nunits * nops * kRow;
+  if (R < 32 && cols >= kPipeMinCols) {
+    constexpr int S = kColsPerThread;
+    const unsigned blocks = (unsigned)(((cols + S - 1) / S + 255) / 256);
+    k_col_fwd<R, S><<<blocks, 256, 0, st>>>(P, nops);
+  } else {
+    k_col_fwd<R, 1><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
+  }
   return cudaGetLastError();
 }
 
 template <int R>
 static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
-  constexpr int S = (R >= 32) ? 1 : kColsPerThread;
-  const size_t threads = ((size_t)P.nunits * kRow + S - 1) / S;
-  const unsigned blocks = (unsigned)((threads + 255) / 256);
-  if (P.halving)
-    k_col_inv<R, S, true><<<blocks, 256, 0, st>>>(P);
-  else
-    k_col_inv<R, S, false><<<blocks, 256, 0, st>>>(P);
+  const size_t cols = (size_t)P.nunits * kRow;
+  const bool pipe = R < 32 && cols >= kPipeMinCols;
+  constexpr int S = kColsPerThread;
+  const unsigned blocks = (unsigned)((((pipe ? (cols + S - 1) / S : cols)) + 255) / 256);
+  if (pipe) {
+    if (P.halving)
+      k_col_inv<R, S, true><<<blocks, 256, 0, st>>>(P);
+    else
+      k_col_inv<R, S, false><<<blocks, 256, 0, st>>>(P);
+  } else {
+    if (P.halving)
+      k_col_inv<R, 1, true><<<blocks, 256, 0, st>>>(P);
+    else
+      k_col_inv<R, 1, false><<<blocks, 256, 0, st>>>(P);
+  }
   return cudaGetLastError();
 }
 
