@@ -221,6 +221,42 @@ pm_status pm_polymul_uneven(pm_queue *q, const pm_job *jobs, uint32_t njobs, voi
  * queue gave up waiting for a dependency. */
 pm_status pm_queue_sync(pm_queue *q, void *stream);
 
+/* ---- Serving: a continuous-batching request loop.
+ * Clients submit products whose operands are already on the device; a
+ * worker thread forms batches from queued requests in arrival order,
+ * admitting a request only when its output (npoly * nlimbs * N words) and
+ * column-stage scratch (as many words again for N >= 2^13 unless a == b)
+ * fit in the remaining budget of a device arena allocated once at creation,
+ * and runs each batch as one uneven persistent launch.  Up to max_inflight
+ * batches are on the device at once (one stream each), so requests arriving
+ * while others run are admitted as soon as a slot and memory free up.
+ * A request's output stays in the arena until pm_server_release(). */
+typedef struct pm_server pm_server;
+typedef struct pm_server_config {
+    uint64_t hbm_budget_bytes;  /* arena size: the admission cap */
+    uint32_t max_batch;         /* requests per launch, 0 = no cap */
+    uint32_t max_inflight;      /* batches on the device at once, 1..8 */
+} pm_server_config;
+typedef struct pm_server_stats {
+    uint64_t submitted, completed, batches, batched_requests, max_batch;
+    uint64_t arena_peak_bytes, arena_used_bytes;
+} pm_server_stats;
+
+pm_status pm_server_create(pm_server **out, int device, const pm_server_config *cfg);
+/* Drains queued and running requests, then frees everything. */
+pm_status pm_server_destroy(pm_server *s);
+/* Queue one request (npoly products of `plan`); PM_ERR_BUDGET if it could
+ * never fit.  d_a, d_b must stay valid until the request is done. */
+pm_status pm_server_submit(pm_server *s, const pm_plan *plan, const uint64_t *d_a,
+                           const uint64_t *d_b, uint32_t npoly, uint64_t *id_out);
+/* Block until request `id` is done (PM_ERR_TIMEOUT after timeout_ms); gives
+ * its device output [npoly][nlimbs][N] and submit-to-completion latency. */
+pm_status pm_server_wait(pm_server *s, uint64_t id, uint32_t timeout_ms, uint64_t **d_c_out,
+                         double *latency_us);
+/* Return a done request's output memory to the arena. */
+pm_status pm_server_release(pm_server *s, uint64_t id);
+pm_status pm_server_get_stats(pm_server *s, pm_server_stats *out);
+
 /* Checks 0 <= x < q_l for every coefficient of d_x [npoly][nlimbs][N];
  * returns PM_ERR_RANGE if one is out of range.  Synchronous. */
 pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t npoly,

@@ -52,6 +52,13 @@ SIGNATURES = {
     "pm_graph_create_polymul": (_i32, [ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _u32]),
     "pm_graph_launch": (_i32, [_vp, _vp]),
     "pm_graph_destroy": (_i32, [_vp]),
+    "pm_server_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_void_p]),
+    "pm_server_destroy": (_i32, [_vp]),
+    "pm_server_submit": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.POINTER(ctypes.c_uint64)]),
+    "pm_server_wait": (_i32, [_vp, _u64, _u32, ctypes.POINTER(ctypes.c_void_p),
+                              ctypes.POINTER(ctypes.c_double)]),
+    "pm_server_release": (_i32, [_vp, _u64]),
+    "pm_server_get_stats": (_i32, [_vp, ctypes.c_void_p]),
     "pm_queue_create": (_i32, [ctypes.POINTER(_vp), _i32]),
     "pm_queue_destroy": (_i32, [_vp]),
     "pm_queue_reserve": (_i32, [_vp, _u64, _u64]),
@@ -283,6 +290,54 @@ def pm_polymul_uneven(q: int, jobs, stream: int = 0) -> None:
 
 def pm_queue_sync(q: int, stream: int = 0) -> None:
     _call("pm_queue_sync", q, stream)
+
+
+class PmServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32)]
+
+
+class PmServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("submitted", "completed", "batches", "batched_requests", "max_batch",
+                 "arena_peak_bytes", "arena_used_bytes")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+def pm_server_create(device: int, budget_bytes: int, max_batch: int = 0, max_inflight: int = 2) -> int:
+    cfg = PmServerConfig(budget_bytes, max_batch, max_inflight)
+    out = ctypes.c_void_p()
+    _call("pm_server_create", ctypes.byref(out), device, ctypes.byref(cfg))
+    return out.value
+
+
+def pm_server_destroy(s: int) -> None:
+    _call("pm_server_destroy", s)
+
+
+def pm_server_submit(s: int, plan: int, d_a: int, d_b: int, npoly: int) -> int:
+    rid = ctypes.c_uint64()
+    _call("pm_server_submit", s, plan, d_a, d_b, npoly, ctypes.byref(rid))
+    return rid.value
+
+
+def pm_server_wait(s: int, rid: int, timeout_ms: int = 60000):
+    """(device pointer of the output, latency in microseconds)."""
+    ptr, lat = ctypes.c_void_p(), ctypes.c_double()
+    _call("pm_server_wait", s, rid, timeout_ms, ctypes.byref(ptr), ctypes.byref(lat))
+    return ptr.value, lat.value
+
+
+def pm_server_release(s: int, rid: int) -> None:
+    _call("pm_server_release", s, rid)
+
+
+def pm_server_get_stats(s: int) -> dict:
+    st = PmServerStats()
+    _call("pm_server_get_stats", s, ctypes.byref(st))
+    return st.as_dict()
 
 
 def pm_version() -> str:

@@ -2,12 +2,18 @@
 // validation, error reporting and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <chrono>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <mutex>
 #include <new>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pm.h"
@@ -770,6 +776,120 @@ pm_status queue_reserve(pm_queue* q, size_t units, size_t scratch_words) {
 
 }  // namespace
 
+// The uneven launch.  ext_scratch[j], when given, is job j's own column-stage
+// scratch (npoly * nlimbs * N words, for N >= 2^13 and a != b); otherwise the
+// queue's scratch is used.  The caller holds q->mu with q's device current.
+pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t* const* ext_scratch,
+                      cudaStream_t st) {
+  if (!q) return fail(PM_ERR_ARG, "queue is NULL");
+  if (njobs == 0) return ok();
+  if (!jobs) return fail(PM_ERR_ARG, "jobs is NULL");
+  // validate and size
+  uint64_t units = 0, scratch = 0;
+  int halving = -1;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
+    if (J.plan->device != q->device)
+      return fail(PM_ERR_ARG, "job %u: plan on device %d, queue on %d", j, J.plan->device, q->device);
+    if (J.npoly == 0) return fail(PM_ERR_ARG, "job %u: npoly is 0", j);
+    if (!J.a || !J.b || !J.c || !aligned16(J.a) || !aligned16(J.b) || !aligned16(J.c))
+      return fail(PM_ERR_ARG, "job %u: NULL or misaligned pointer", j);
+    if (J.plan->logn < 12) continue;  // run through the plan's own path below
+    const int h = (J.plan->flags & PM_PLAN_HALVING) ? 1 : 0;
+    if (halving >= 0 && h != halving)
+      return fail(PM_ERR_ARG, "jobs mix PM_PLAN_HALVING and default plans");
+    halving = h;
+    const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
+    units += u;
+    if (J.plan->logn > 12 && J.a != J.b && !(ext_scratch && ext_scratch[j]))
+      scratch += u << J.plan->logn;
+  }
+  if (units > 0x3fffffffull) return fail(PM_ERR_ARG, "too many units (%llu)", (unsigned long long)units);
+  cudaError_t e;
+  // small-N jobs: their plan's own path, on the same stream
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    if (J.plan->logn >= 12) continue;
+    pm_plan* p = const_cast<pm_plan*>(J.plan);
+    std::lock_guard<std::mutex> lp(p->mu);
+    pm_status s2 = polymul_impl(p, J.a, J.b, J.c, J.npoly, st);
+    if (s2 != PM_OK) return s2;
+  }
+  if (units == 0) return ok();
+  pm_status s = queue_reserve(q, units, scratch ? scratch : 1);
+  if (s != PM_OK) return s;
+  if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
+    return cuda_fail(e, "queue staging");
+  // unit descriptors and section prefix counts
+  uint32_t* pf = q->h_pre;
+  uint32_t* pw = q->h_pre + units;
+  uint32_t* pi = q->h_pre + 2 * units;
+  uint32_t tf = 0, tw = 0, ti = 0;
+  uint64_t soff = 0;
+  size_t u = 0;
+  for (uint32_t j = 0; j < njobs; ++j) {
+    const pm_job& J = jobs[j];
+    const pm_plan* p = J.plan;
+    if (p->logn < 12) continue;
+    const uint64_t n = (uint64_t)1 << p->logn;
+    const bool split = p->logn > 12;
+    const bool square = J.a == J.b;
+    uint64_t* own = (ext_scratch && ext_scratch[j]) ? ext_scratch[j] : nullptr;
+    for (uint32_t k = 0; k < J.npoly * p->nlimbs; ++k, ++u) {
+      pm::UnitDesc& D = q->h_units[u];
+      const uint32_t limb = k % p->nlimbs;
+      D.a = J.a + k * n;
+      D.b = J.b + k * n;
+      D.c = J.c + k * n;
+      if (split && !square) {
+        if (own) {
+          D.s = own + k * n;
+        } else {
+          D.s = q->d_scratch + soff;
+          soff += n;
+        }
+        if (J.c == J.b) std::swap(D.a, D.b);  // b's image stays in place in c
+      } else {
+        D.s = D.c;
+      }
+      D.twf = p->d_twf + ((size_t)limb << p->logn);
+      D.twi = p->d_twi + ((size_t)limb << p->logn);
+      D.lc = p->d_lc + limb;
+      D.logn = p->logn;
+      D.pad = 0;
+      pf[u] = tf;
+      pw[u] = tw;
+      pi[u] = ti;
+      tf += split ? (square ? 1u : 2u) * 16u : 0u;
+      tw += (uint32_t)(n >> 12);
+      ti += split ? 16u : 0u;
+    }
+  }
+  // the three prefix arrays are uploaded contiguously, in the order f, w, i
+  if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(q->d_pre, q->h_pre, 3 * units * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess ||
+      (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
+    return cuda_fail(e, "queue upload");
+  q->staged_used = true;
+  pm::UnevenArgs A{};
+  A.units = q->d_units;
+  A.pre_f = q->d_pre;
+  A.pre_w = q->d_pre + units;
+  A.pre_i = q->d_pre + 2 * units;
+  A.ctl = q->d_ctl;
+  A.nunits = (uint32_t)units;
+  A.tf = tf;
+  A.tw = tw;
+  A.ti = ti;
+  if ((e = pm::launch_uneven(A, halving == 1, q->num_sms * 3, st)) != cudaSuccess)
+    return cuda_fail(e, "uneven launch");
+  return ok();
+}
+
+
 extern "C" {
 
 pm_status pm_queue_create(pm_queue** out, int device) {
@@ -812,109 +932,10 @@ pm_status pm_queue_reserve(pm_queue* q, uint64_t units, uint64_t scratch_words) 
 
 pm_status pm_polymul_uneven(pm_queue* q, const pm_job* jobs, uint32_t njobs, void* stream) {
   if (!q) return fail(PM_ERR_ARG, "queue is NULL");
-  if (njobs == 0) return ok();
-  if (!jobs) return fail(PM_ERR_ARG, "jobs is NULL");
-  // validate and size
-  uint64_t units = 0, scratch = 0;
-  int halving = -1;
-  for (uint32_t j = 0; j < njobs; ++j) {
-    const pm_job& J = jobs[j];
-    if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
-    if (J.plan->device != q->device)
-      return fail(PM_ERR_ARG, "job %u: plan on device %d, queue on %d", j, J.plan->device, q->device);
-    if (J.npoly == 0) return fail(PM_ERR_ARG, "job %u: npoly is 0", j);
-    if (!J.a || !J.b || !J.c || !aligned16(J.a) || !aligned16(J.b) || !aligned16(J.c))
-      return fail(PM_ERR_ARG, "job %u: NULL or misaligned pointer", j);
-    if (J.plan->logn < 12) continue;  // run through the plan's own path below
-    const int h = (J.plan->flags & PM_PLAN_HALVING) ? 1 : 0;
-    if (halving >= 0 && h != halving)
-      return fail(PM_ERR_ARG, "jobs mix PM_PLAN_HALVING and default plans");
-    halving = h;
-    const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
-    units += u;
-    if (J.plan->logn > 12 && J.a != J.b) scratch += u << J.plan->logn;
-  }
-  if (units > 0x3fffffffull) return fail(PM_ERR_ARG, "too many units (%llu)", (unsigned long long)units);
   DeviceGuard g(q->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   std::lock_guard<std::mutex> lk(q->mu);
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e;
-  // small-N jobs: their plan's own path, on the same stream
-  for (uint32_t j = 0; j < njobs; ++j) {
-    const pm_job& J = jobs[j];
-    if (J.plan->logn >= 12) continue;
-    pm_plan* p = const_cast<pm_plan*>(J.plan);
-    std::lock_guard<std::mutex> lp(p->mu);
-    pm_status s2 = polymul_impl(p, J.a, J.b, J.c, J.npoly, st);
-    if (s2 != PM_OK) return s2;
-  }
-  if (units == 0) return ok();
-  pm_status s = queue_reserve(q, units, scratch ? scratch : 1);
-  if (s != PM_OK) return s;
-  if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
-    return cuda_fail(e, "queue staging");
-  // unit descriptors and section prefix counts
-  uint32_t* pf = q->h_pre;
-  uint32_t* pw = q->h_pre + units;
-  uint32_t* pi = q->h_pre + 2 * units;
-  uint32_t tf = 0, tw = 0, ti = 0;
-  uint64_t soff = 0;
-  size_t u = 0;
-  for (uint32_t j = 0; j < njobs; ++j) {
-    const pm_job& J = jobs[j];
-    const pm_plan* p = J.plan;
-    if (p->logn < 12) continue;
-    const uint64_t n = (uint64_t)1 << p->logn;
-    const bool split = p->logn > 12;
-    const bool square = J.a == J.b;
-    for (uint32_t k = 0; k < J.npoly * p->nlimbs; ++k, ++u) {
-      pm::UnitDesc& D = q->h_units[u];
-      const uint32_t limb = k % p->nlimbs;
-      D.a = J.a + k * n;
-      D.b = J.b + k * n;
-      D.c = J.c + k * n;
-      if (split && !square) {
-        D.s = q->d_scratch + soff;
-        soff += n;
-        if (J.c == J.b) std::swap(D.a, D.b);  // b's image stays in place in c
-      } else {
-        D.s = D.c;
-      }
-      D.twf = p->d_twf + ((size_t)limb << p->logn);
-      D.twi = p->d_twi + ((size_t)limb << p->logn);
-      D.lc = p->d_lc + limb;
-      D.logn = p->logn;
-      D.pad = 0;
-      pf[u] = tf;
-      pw[u] = tw;
-      pi[u] = ti;
-      tf += split ? (square ? 1u : 2u) * 16u : 0u;
-      tw += (uint32_t)(n >> 12);
-      ti += split ? 16u : 0u;
-    }
-  }
-  // the three prefix arrays are uploaded contiguously, in the order f, w, i
-  if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
-                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(q->d_pre, q->h_pre, 3 * units * sizeof(uint32_t), cudaMemcpyHostToDevice,
-                           st)) != cudaSuccess ||
-      (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
-    return cuda_fail(e, "queue upload");
-  q->staged_used = true;
-  pm::UnevenArgs A{};
-  A.units = q->d_units;
-  A.pre_f = q->d_pre;
-  A.pre_w = q->d_pre + units;
-  A.pre_i = q->d_pre + 2 * units;
-  A.ctl = q->d_ctl;
-  A.nunits = (uint32_t)units;
-  A.tf = tf;
-  A.tw = tw;
-  A.ti = ti;
-  if ((e = pm::launch_uneven(A, halving == 1, q->num_sms * 3, st)) != cudaSuccess)
-    return cuda_fail(e, "uneven launch");
-  return ok();
+  return uneven_impl(q, jobs, njobs, nullptr, (cudaStream_t)stream);
 }
 
 pm_status pm_queue_sync(pm_queue* q, void* stream) {
@@ -1029,6 +1050,367 @@ pm_status pm_graph_launch(pm_graph* g, void* stream) {
 
 pm_status pm_graph_destroy(pm_graph* g) {
   destroy_graph(g);
+  return ok();
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- serving
+//
+// A continuous-batching request loop.  Clients submit products whose
+// operands already live on the device; a worker thread forms batches from
+// the queued requests in arrival order, admitting each one only if its
+// output and column-stage scratch fit in the remaining device-memory budget
+// (an arena allocated once), and runs every batch as one uneven persistent
+// launch.  Up to `max_inflight` batches are on the device at once (one
+// stream and work queue each), so requests that arrive while others run are
+// admitted as soon as a slot and memory free up.  Outputs stay in the arena
+// until the client releases the request.
+
+namespace {
+
+double now_us() {
+  using namespace std::chrono;
+  return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, size) in 256-byte granules.
+struct Arena {
+  std::map<uint64_t, uint64_t> free_;  // offset -> length
+  uint64_t used = 0, peak = 0;
+  void init(uint64_t size) {
+    free_.clear();
+    free_[0] = size;
+    used = peak = 0;
+  }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    bytes = (bytes + 255) & ~(uint64_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const uint64_t rest = it->second - bytes;
+        const uint64_t noff = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[noff] = rest;
+        used += bytes;
+        if (used > peak) peak = used;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~(uint64_t)255;
+    used -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2 };
+
+struct Request {
+  const pm_plan* plan;
+  const uint64_t* a;
+  const uint64_t* b;
+  uint32_t npoly;
+  uint64_t c_off = 0, c_bytes = 0, s_off = 0, s_bytes = 0;
+  double t_submit = 0, t_done = 0;
+  int state = RQ_QUEUED;
+  pm_status status = PM_OK;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  pm_queue* queue = nullptr;
+  bool busy = false;
+  std::vector<uint64_t> ids;
+};
+
+}  // namespace
+
+struct pm_server {
+  int device = 0;
+  pm_server_config cfg{};
+  uint8_t* arena_base = nullptr;
+  Arena arena;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queued;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::vector<Slot> slots;
+  std::thread worker;
+  bool stop = false;
+  uint64_t next_id = 1;
+  pm_server_stats stats{};
+  pm_status worker_status = PM_OK;
+  char worker_msg[256] = "";
+};
+
+namespace {
+
+uint64_t request_scratch_bytes(const pm_plan* p, uint32_t npoly, bool square) {
+  if (p->logn < 13 || square) return 0;
+  return (uint64_t)npoly * p->nlimbs << p->logn << 3;
+}
+
+// Worker: retire finished batches, then launch a new one on a free slot.
+void server_loop(pm_server* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    bool progress = false;
+    for (auto& sl : S->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      const double t = now_us();
+      pm_status st = PM_OK;
+      if (q != cudaSuccess) {
+        st = PM_ERR_CUDA;
+      } else {
+        uint32_t flag = 0;
+        if (sl.queue->d_ctl && cudaMemcpy(&flag, sl.queue->d_ctl + 1, 4, cudaMemcpyDeviceToHost) == cudaSuccess && flag) {
+          st = PM_ERR_TIMEOUT;
+          cudaMemset(sl.queue->d_ctl + 1, 0, 4);
+        }
+      }
+      for (uint64_t id : sl.ids) {
+        Request& r = S->reqs[id];
+        r.state = RQ_DONE;
+        r.status = st;
+        r.t_done = t;
+        if (r.s_bytes) S->arena.release(r.s_off, r.s_bytes);
+        r.s_bytes = 0;
+        S->stats.completed++;
+      }
+      sl.ids.clear();
+      sl.busy = false;
+      progress = true;
+      S->cv_done.notify_all();
+    }
+    Slot* free_slot = nullptr;
+    for (auto& sl : S->slots)
+      if (!sl.busy) {
+        free_slot = &sl;
+        break;
+      }
+    if (free_slot && !S->queued.empty()) {
+      std::vector<pm_job> jobs;
+      std::vector<uint64_t*> scr;
+      std::vector<uint64_t> ids;
+      while (!S->queued.empty() && (!S->cfg.max_batch || ids.size() < S->cfg.max_batch)) {
+        const uint64_t id = S->queued.front();
+        Request& r = S->reqs[id];
+        const bool square = r.a == r.b;
+        const uint64_t cb = (uint64_t)r.npoly * r.plan->nlimbs << r.plan->logn << 3;
+        const uint64_t sb = request_scratch_bytes(r.plan, r.npoly, square);
+        uint64_t coff = 0, soff = 0;
+        if (!S->arena.alloc(cb, &coff)) break;
+        if (sb && !S->arena.alloc(sb, &soff)) {
+          S->arena.release(coff, cb);
+          break;
+        }
+        r.c_off = coff;
+        r.c_bytes = cb;
+        r.s_off = soff;
+        r.s_bytes = sb;
+        r.state = RQ_RUNNING;
+        S->queued.pop_front();
+        jobs.push_back(pm_job{r.plan, r.a, r.b, (uint64_t*)(S->arena_base + coff), r.npoly});
+        scr.push_back(sb ? (uint64_t*)(S->arena_base + soff) : nullptr);
+        ids.push_back(id);
+      }
+      if (!ids.empty()) {
+        pm_status st;
+        {
+          std::lock_guard<std::mutex> lq(free_slot->queue->mu);
+          st = uneven_impl(free_slot->queue, jobs.data(), (uint32_t)jobs.size(), scr.data(),
+                           free_slot->stream);
+        }
+        if (st == PM_OK && cudaEventRecord(free_slot->done, free_slot->stream) != cudaSuccess)
+          st = PM_ERR_CUDA;
+        if (st != PM_OK) {
+          S->worker_status = st;
+          snprintf(S->worker_msg, sizeof(S->worker_msg), "%s", g_err);
+          for (uint64_t id : ids) {
+            Request& r = S->reqs[id];
+            r.state = RQ_DONE;
+            r.status = st;
+            r.t_done = now_us();
+            if (r.s_bytes) S->arena.release(r.s_off, r.s_bytes);
+            r.s_bytes = 0;
+          }
+          S->cv_done.notify_all();
+        } else {
+          free_slot->ids = ids;
+          free_slot->busy = true;
+          S->stats.batches++;
+          S->stats.batched_requests += ids.size();
+          if (ids.size() > S->stats.max_batch) S->stats.max_batch = ids.size();
+        }
+        progress = true;
+      }
+    }
+    S->stats.arena_peak_bytes = S->arena.peak;
+    bool any_busy = false;
+    for (auto& sl : S->slots) any_busy |= sl.busy;
+    if (S->stop && !any_busy && S->queued.empty()) break;
+    if (!progress) {
+      if (any_busy)
+        S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+      else
+        S->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+  }
+}
+
+void destroy_server(pm_server* S) {
+  if (!S) return;
+  if (S->worker.joinable()) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
+    }
+    S->cv_work.notify_all();
+    S->worker.join();
+  }
+  DeviceGuard g(S->device);
+  for (auto& sl : S->slots) {
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+    destroy_queue(sl.queue);
+  }
+  cudaFree(S->arena_base);
+  delete S;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_server_create(pm_server** out, int device, const pm_server_config* cfg) {
+  if (!out || !cfg) return fail(PM_ERR_ARG, "out or cfg is NULL");
+  *out = nullptr;
+  if (cfg->hbm_budget_bytes < (1u << 20)) return fail(PM_ERR_ARG, "budget below 1 MiB");
+  if (cfg->max_inflight < 1 || cfg->max_inflight > 8) return fail(PM_ERR_ARG, "max_inflight must be 1..8");
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(PM_ERR_ARG, "device %d not present", device);
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_server* S = new (std::nothrow) pm_server();
+  if (!S) return fail(PM_ERR_OOM, "host allocation failed");
+  S->device = device;
+  S->cfg = *cfg;
+  if ((e = cudaMalloc(&S->arena_base, cfg->hbm_budget_bytes)) != cudaSuccess) {
+    destroy_server(S);
+    return cuda_fail(e, "cudaMalloc(serving arena)");
+  }
+  S->arena.init(cfg->hbm_budget_bytes);
+  S->slots.resize(cfg->max_inflight);
+  for (auto& sl : S->slots) {
+    pm_status st = pm_queue_create(&sl.queue, device);
+    if (st != PM_OK) {
+      destroy_server(S);
+      return st;
+    }
+    if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) {
+      destroy_server(S);
+      return cuda_fail(e, "serving streams");
+    }
+  }
+  S->worker = std::thread(server_loop, S);
+  *out = S;
+  return ok();
+}
+
+pm_status pm_server_destroy(pm_server* S) {
+  destroy_server(S);
+  return ok();
+}
+
+pm_status pm_server_submit(pm_server* S, const pm_plan* plan, const uint64_t* d_a,
+                           const uint64_t* d_b, uint32_t npoly, uint64_t* id_out) {
+  if (!S || !plan || !id_out) return fail(PM_ERR_ARG, "NULL argument");
+  if (!d_a || !d_b || !aligned16(d_a) || !aligned16(d_b)) return fail(PM_ERR_ARG, "NULL or misaligned operand");
+  if (plan->device != S->device) return fail(PM_ERR_ARG, "plan on another device");
+  pm_status s = check_batch(plan, npoly);
+  if (s != PM_OK) return s;
+  const uint64_t need = ((uint64_t)npoly * plan->nlimbs << plan->logn << 3) +
+                        request_scratch_bytes(plan, npoly, d_a == d_b) + 512;
+  if (need > S->cfg.hbm_budget_bytes)
+    return fail(PM_ERR_BUDGET, "request needs %llu bytes, budget is %llu", (unsigned long long)need,
+                (unsigned long long)S->cfg.hbm_budget_bytes);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return fail(PM_ERR_ARG, "server is stopping");
+    const uint64_t id = S->next_id++;
+    Request r;
+    r.plan = plan;
+    r.a = d_a;
+    r.b = d_b;
+    r.npoly = npoly;
+    r.t_submit = now_us();
+    S->reqs.emplace(id, r);
+    S->queued.push_back(id);
+    S->stats.submitted++;
+    *id_out = id;
+  }
+  S->cv_work.notify_one();
+  return ok();
+}
+
+pm_status pm_server_wait(pm_server* S, uint64_t id, uint32_t timeout_ms, uint64_t** d_c_out,
+                         double* latency_us) {
+  if (!S) return fail(PM_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(PM_ERR_ARG, "unknown request %llu", (unsigned long long)id);
+  const bool ready = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+    return S->reqs[id].state == RQ_DONE;
+  });
+  if (!ready) return fail(PM_ERR_TIMEOUT, "request %llu not done within %u ms", (unsigned long long)id, timeout_ms);
+  Request& r = S->reqs[id];
+  if (r.status != PM_OK) return fail(r.status, "request %llu failed: %s", (unsigned long long)id, S->worker_msg);
+  if (d_c_out) *d_c_out = (uint64_t*)(S->arena_base + r.c_off);
+  if (latency_us) *latency_us = r.t_done - r.t_submit;
+  return ok();
+}
+
+pm_status pm_server_release(pm_server* S, uint64_t id) {
+  if (!S) return fail(PM_ERR_ARG, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return fail(PM_ERR_ARG, "unknown request %llu", (unsigned long long)id);
+    if (it->second.state != RQ_DONE) return fail(PM_ERR_ARG, "request %llu still running", (unsigned long long)id);
+    if (it->second.c_bytes) S->arena.release(it->second.c_off, it->second.c_bytes);
+    S->reqs.erase(it);
+  }
+  S->cv_work.notify_one();
+  return ok();
+}
+
+pm_status pm_server_get_stats(pm_server* S, pm_server_stats* out) {
+  if (!S || !out) return fail(PM_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  *out = S->stats;
+  out->arena_used_bytes = S->arena.used;
   return ok();
 }
 
