@@ -484,9 +484,82 @@ def run_workload(args):
                       "one_launch_speedup": float(np.median(t2)) / float(np.median(t1)),
                       "one_launch_polymuls_per_s": units / (float(np.median(t1)) * 1e-3),
                       "one_launch_tmulmod_per_s": mm / (float(np.median(t1)) * 1e-3) / 1e12})
+    elif args.workload == "c5":
+        lines.append(run_serving(args, dev))
     for line in lines:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def run_serving(args, dev):
+    """Poisson request stream through the continuous-batching server."""
+    import threading
+    import torch
+    from paper_2209_01290_gb300 import Plan, capi, inputs
+    rate, seconds = args.serve_rate, args.serve_seconds
+    choices, weights, max_l = (13, 15, 16), (0.3, 0.4, 0.3), 32
+    reqs = inputs.poisson_requests(inputs.seed_for(4), rate, seconds, choices, weights, max_l)
+    plans, pool = {}, {}
+    for ln in choices:
+        for L in range(1, max_l + 1):
+            qs, psis = capi.pm_find_params(ln, L, 60)
+            plans[(ln, L)] = Plan(1 << ln, qs, psis, device=dev)
+            a = inputs.uniform_limbs_torch(ln * 100 + L, qs, 1, 1 << ln, device=dev)
+            b = inputs.uniform_limbs_torch(ln * 100 + L + 50, qs, 1, 1 << ln, device=dev)
+            pool[(ln, L)] = (a, b)
+    torch.cuda.synchronize(dev)
+    srv = capi.pm_server_create(dev, args.serve_budget_gb << 30, 0, 2)
+    ids = [0] * len(reqs)
+    lag = [0.0] * len(reqs)
+    submitted = threading.Event()
+    n_sub = [0]
+
+    def producer():
+        t0 = time.perf_counter()
+        for i, r in enumerate(reqs):
+            target = t0 + r.arrival_s
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 2e-4:
+                    time.sleep(5e-5)
+            a, b = pool[(r.log2n, r.nlimbs)]
+            ids[i] = capi.pm_server_submit(srv, plans[(r.log2n, r.nlimbs)].handle,
+                                           a.data_ptr(), b.data_ptr(), 1)
+            lag[i] = time.perf_counter() - target
+            n_sub[0] = i + 1
+        submitted.set()
+
+    lat = []
+    th = threading.Thread(target=producer)
+    t_start = time.perf_counter()
+    th.start()
+    for i in range(len(reqs)):
+        while n_sub[0] <= i:
+            time.sleep(1e-4)
+        _, l_us = capi.pm_server_wait(srv, ids[i], 600000)
+        lat.append(l_us)
+        capi.pm_server_release(srv, ids[i])
+    t_end = time.perf_counter()
+    th.join()
+    st = capi.pm_server_get_stats(srv)
+    capi.pm_server_destroy(srv)
+    units = sum(r.nlimbs for r in reqs)
+    mm = sum(mulmods_per_polymul(r.log2n) * r.nlimbs for r in reqs)
+    span = t_end - t_start
+    lat = np.array(lat)
+    return {"workload": f"c5: Poisson {rate:.0f} req/s for {seconds:.0f} s, N in 2^13/2^15/2^16 "
+                        f"(0.3/0.4/0.3), 1..32 limbs, device-resident operands, "
+                        f"{args.serve_budget_gb} GB budget",
+            "requests": len(reqs), "latency_p50_us": float(np.percentile(lat, 50)),
+            "latency_p99_us": float(np.percentile(lat, 99)),
+            "latency_max_us": float(lat.max()),
+            "achieved_requests_per_s": len(reqs) / span, "offered_requests_per_s": rate,
+            "achieved_polymuls_per_s": units / span, "achieved_tmulmod_per_s": mm / span / 1e12,
+            "generator_lag_p99_us": float(np.percentile(np.array(lag), 99) * 1e6),
+            "batches": st["batches"], "mean_batch": st["batched_requests"] / max(1, st["batches"]),
+            "max_batch": st["max_batch"], "arena_peak_gib": st["arena_peak_bytes"] / 2**30}
 
 
 def main():
@@ -501,7 +574,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
-    ap.add_argument("--workload", default="headline", choices=["headline", "c1", "c2sweep", "c3", "c4"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "c1", "c2sweep", "c3", "c4", "c5"])
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--ctas-per-sm", type=int, default=3)
     ap.add_argument("--lag-fwd", type=int, default=8)
     ap.add_argument("--lag-inv", type=int, default=16)
