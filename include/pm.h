@@ -236,6 +236,10 @@ typedef struct pm_server_config {
     uint64_t hbm_budget_bytes;  /* arena size: the admission cap */
     uint32_t max_batch;         /* requests per launch, 0 = no cap */
     uint32_t max_inflight;      /* batches on the device at once, 1..8 */
+    uint64_t min_batch_rows;    /* while a batch runs, launch the next only once
+                                   the queue holds this many 4096-word rows of
+                                   work; 0 = 4 x 3 x SM count.  An idle device
+                                   always takes what is queued. */
 } pm_server_config;
 typedef struct pm_server_stats {
     uint64_t submitted, completed, batches, batched_requests, max_batch;

@@ -294,7 +294,7 @@ def pm_queue_sync(q: int, stream: int = 0) -> None:
 
 class PmServerConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32)]
+                ("max_inflight", ctypes.c_uint32), ("min_batch_rows", ctypes.c_uint64)]
 
 
 class PmServerStats(ctypes.Structure):
@@ -306,8 +306,9 @@ class PmServerStats(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
-def pm_server_create(device: int, budget_bytes: int, max_batch: int = 0, max_inflight: int = 2) -> int:
-    cfg = PmServerConfig(budget_bytes, max_batch, max_inflight)
+def pm_server_create(device: int, budget_bytes: int, max_batch: int = 0, max_inflight: int = 2,
+                     min_batch_rows: int = 0) -> int:
+    cfg = PmServerConfig(budget_bytes, max_batch, max_inflight, min_batch_rows)
     out = ctypes.c_void_p()
     _call("pm_server_create", ctypes.byref(out), device, ctypes.byref(cfg))
     return out.value

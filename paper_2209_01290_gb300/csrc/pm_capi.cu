@@ -1154,6 +1154,8 @@ struct pm_server {
   std::thread worker;
   bool stop = false;
   uint64_t next_id = 1;
+  uint64_t queued_rows = 0;   // row tasks (4096-word rows) of the queued requests
+  uint64_t min_rows = 0;      // launch threshold while another batch runs
   pm_server_stats stats{};
   pm_status worker_status = PM_OK;
   char worker_msg[256] = "";
@@ -1164,6 +1166,12 @@ namespace {
 uint64_t request_scratch_bytes(const pm_plan* p, uint32_t npoly, bool square) {
   if (p->logn < 13 || square) return 0;
   return (uint64_t)npoly * p->nlimbs << p->logn << 3;
+}
+
+// Work of a request in 4096-word rows (a request of smaller N counts as one).
+uint64_t request_rows(const pm_plan* p, uint32_t npoly) {
+  const uint64_t per = p->logn > 12 ? ((uint64_t)1 << (p->logn - 12)) : 1;
+  return (uint64_t)npoly * p->nlimbs * per;
 }
 
 // Worker: retire finished batches, then launch a new one on a free slot.
@@ -1202,12 +1210,16 @@ void server_loop(pm_server* S) {
       S->cv_done.notify_all();
     }
     Slot* free_slot = nullptr;
-    for (auto& sl : S->slots)
-      if (!sl.busy) {
+    bool running = false;
+    for (auto& sl : S->slots) {
+      if (sl.busy)
+        running = true;
+      else if (!free_slot)
         free_slot = &sl;
-        break;
-      }
-    if (free_slot && !S->queued.empty()) {
+    }
+    // An idle device takes whatever is queued; while a batch runs, the next
+    // one waits until it has enough rows to keep the GPU full on its own.
+    if (free_slot && !S->queued.empty() && (!running || S->queued_rows >= S->min_rows)) {
       std::vector<pm_job> jobs;
       std::vector<uint64_t*> scr;
       std::vector<uint64_t> ids;
@@ -1229,6 +1241,7 @@ void server_loop(pm_server* S) {
         r.s_bytes = sb;
         r.state = RQ_RUNNING;
         S->queued.pop_front();
+        S->queued_rows -= request_rows(r.plan, r.npoly);
         jobs.push_back(pm_job{r.plan, r.a, r.b, (uint64_t*)(S->arena_base + coff), r.npoly});
         scr.push_back(sb ? (uint64_t*)(S->arena_base + soff) : nullptr);
         ids.push_back(id);
@@ -1321,6 +1334,9 @@ pm_status pm_server_create(pm_server** out, int device, const pm_server_config* 
     return cuda_fail(e, "cudaMalloc(serving arena)");
   }
   S->arena.init(cfg->hbm_budget_bytes);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  S->min_rows = cfg->min_batch_rows ? cfg->min_batch_rows : (uint64_t)sms * 3 * 4;
   S->slots.resize(cfg->max_inflight);
   for (auto& sl : S->slots) {
     pm_status st = pm_queue_create(&sl.queue, device);
@@ -1368,6 +1384,7 @@ pm_status pm_server_submit(pm_server* S, const pm_plan* plan, const uint64_t* d_
     r.t_submit = now_us();
     S->reqs.emplace(id, r);
     S->queued.push_back(id);
+    S->queued_rows += request_rows(plan, npoly);
     S->stats.submitted++;
     *id_out = id;
   }
