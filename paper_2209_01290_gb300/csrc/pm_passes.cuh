@@ -13,9 +13,12 @@ namespace pm {
 
 constexpr int kRowLog = 12;
 constexpr int kRow = 1 << kRowLog;        // 4096 words per row
-constexpr int kRowPad = kRow + kRow / 32;  // one pad word per 32: conflict-free passes
+// One pad word after every 16: 64-bit shared accesses are served per
+// half-warp, and with this padding the 16 lanes of a half-warp hit 16
+// different bank pairs in every thread layout used below.
+constexpr int kRowPad = kRow + kRow / 16;
 
-__device__ __forceinline__ int padj(int j) { return j + (j >> 5); }
+__device__ __forceinline__ int padj(int j) { return j + (j >> 4); }
 
 // ------------------------------------------------------------------ passes
 
@@ -188,7 +191,7 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
 //   layout 0: j = th + 256 u                      (CT stages n-12.., GS 8..11)
 //   layout 1: j = 256 (th>>4) + (th&15) + 16 u    (CT stages n-8..,  GS 4..7)
 //   layout 2: j = 16 th + u                       (CT stages n-4..,  GS 0..3)
-// are all bank-conflict free with the 1-in-32 padding.  The pass loop is
+// are all bank-conflict free with the 1-in-16 padding.  The pass loop is
 // not unrolled: one copy of the radix-16 body serves all passes, which keeps
 // the kernel small enough for the instruction cache.
 struct PassGeo {
@@ -197,25 +200,25 @@ struct PassGeo {
   uint32_t g;    // block index of the group within the whole transform
 };
 
-// With the 1-in-32 padding p(j) = j + (j >> 5), the padded index of word u
-// of a group is pbase + off(u) with a compile-time offset per layout:
-//   layout 0: 264 u;  layout 1: 16 u + (u >> 1);  layout 2: u.
+// With the padding p(j) = j + (j >> 4), the padded index of word u of a
+// group is pbase + off(u) with a compile-time offset per layout:
+//   layout 0: 272 u;  layout 1: 17 u;  layout 2: u.
 template <int L>
 __device__ __forceinline__ constexpr int lay_off(int u) {
-  return L == 0 ? 264 * u : (L == 1 ? 16 * u + (u >> 1) : u);
+  return L == 0 ? 272 * u : (L == 1 ? 17 * u : u);
 }
 
 __device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
   PassGeo G;
   G.layout = layout;
   if (layout == 0) {
-    G.pbase = th + (th >> 5);
+    G.pbase = th + (th >> 4);
     G.g = t;
   } else if (layout == 1) {
-    G.pbase = 264 * (th >> 4) + (th & 15);
+    G.pbase = 272 * (th >> 4) + (th & 15);
     G.g = t * 16 + (th >> 4);
   } else {
-    G.pbase = 16 * th + (th >> 1);
+    G.pbase = 17 * th;
     G.g = t * 256 + th;
   }
   return G;
