@@ -280,7 +280,13 @@ __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_sr
     ct16(v, twf, logn - 12 + 4 * p, G.g, q, two_q);
     if (p < 2) {
       st_smem16(s, G, v);
-      __syncthreads();
+      // pass 1 -> 2 stays inside a half-warp: the layout-1 block g of 256
+      // words is owned by threads 16g..16g+15, which are exactly the layout-2
+      // threads that read it; pass 0 -> 1 crosses warps.
+      if (p == 0)
+        __syncthreads();
+      else
+        __syncwarp();
     }
   }
 }
@@ -302,7 +308,11 @@ __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, boo
     gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq);
     if (p < 2) {
       st_smem16(s, G, v);
-      __syncthreads();
+      // layout 2 -> 1 stays inside a half-warp, layout 1 -> 0 crosses warps
+      if (p == 0)
+        __syncwarp();
+      else
+        __syncthreads();
     }
   }
   if (g_dst) {
@@ -343,7 +353,10 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
     if (p < 2) {
       st_smem16(sa, G, va);
       st_smem16(sb, G, vb);
-      __syncthreads();
+      if (p == 0)
+        __syncthreads();
+      else
+        __syncwarp();
     }
   }
 }
