@@ -290,6 +290,14 @@ typedef struct pm_tuning {
     uint32_t row_ops;
 } pm_tuning;
 
+/* Autotuner: time every launch choice for batches of `npoly` polynomials
+ * (the split path with each row kernel, the persistent launch with a few
+ * pipeline distances) on temporary device buffers, keep the fastest in the
+ * plan and return it (and its median time in ms).  Allocates, synchronises
+ * `stream`; call it at setup, not on a hot path. */
+pm_status pm_plan_autotune(pm_plan *plan, uint32_t npoly, void *stream, pm_tuning *best_out,
+                           float *best_ms_out);
+
 /* Set / read the plan's launch choice.  PM_ERR_ARG for out-of-range values. */
 pm_status pm_plan_tune(pm_plan *plan, const pm_tuning *t);
 pm_status pm_plan_get_tuning(const pm_plan *plan, pm_tuning *t);

@@ -42,6 +42,7 @@ SIGNATURES = {
     "pm_plan_sync": (_i32, [_vp, _vp]),
     "pm_plan_tune": (_i32, [_vp, ctypes.c_void_p]),
     "pm_plan_inject_fault": (_i32, [_vp, _i32]),
+    "pm_plan_autotune": (_i32, [_vp, _u32, _vp, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "pm_plan_get_tuning": (_i32, [_vp, ctypes.c_void_p]),
     "pm_plan_set_phase_events": (_i32, [_vp, ctypes.POINTER(_vp), _i32]),
     "pm_last_error": (ctypes.c_char_p, []),
@@ -218,6 +219,13 @@ def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 3, lag_fwd: int = 8
                  lag_inv: int = 64, row_ops: int = 1) -> None:
     t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv, row_ops)
     _call("pm_plan_tune", plan, ctypes.byref(t))
+
+
+def pm_plan_autotune(plan: int, npoly: int, stream: int = 0):
+    """Time the launch choices for this batch size; returns (PmTuning, ms)."""
+    t, ms = PmTuning(), ctypes.c_float()
+    _call("pm_plan_autotune", plan, npoly, stream, ctypes.byref(t), ctypes.byref(ms))
+    return t, ms.value
 
 
 PM_FAULT_WITHHOLD_SIGNAL = 1

@@ -2,6 +2,7 @@
 // validation, error reporting and dispatch to the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdarg>
@@ -679,6 +680,71 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
     return fail(PM_ERR_ARG, "persistent tuning needs 1 <= ctas_per_sm <= 3, 1 <= lag_fwd < lag_inv <= 4096");
   std::lock_guard<std::mutex> lk(plan->mu);
   plan->tune = *t;
+  return ok();
+}
+
+pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tuning* best_out,
+                           float* best_ms_out) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  // candidates: the split path with either row kernel, the persistent launch
+  // with a few pipeline distances
+  std::vector<pm_tuning> cand;
+  cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
+  if (plan->logn >= 14) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
+  if (plan->logn >= 13) {
+    cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
+    cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});
+  }
+  const size_t words = (size_t)npoly * plan->nlimbs << plan->logn;
+  uint64_t *a = nullptr, *b = nullptr, *c = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  pm_tuning best = plan->tune;
+  float best_ms = 1e30f;
+  if ((e = cudaMalloc(&a, words * 8)) != cudaSuccess || (e = cudaMalloc(&b, words * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&c, words * 8)) != cudaSuccess || (e = cudaMemsetAsync(a, 0, words * 8, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(b, 0, words * 8, st)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+      (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    s = cuda_fail(e, "autotune buffers");
+  } else {
+    std::lock_guard<std::mutex> lk(plan->mu);
+    const pm_tuning saved = plan->tune;
+    for (const pm_tuning& t : cand) {
+      plan->tune = t;
+      float times[5];
+      for (int r = 0; r < 7 && s == PM_OK; ++r) {
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { s = cuda_fail(e, "event"); break; }
+        if ((s = polymul_impl(plan, a, b, c, npoly, st)) != PM_OK) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+          s = cuda_fail(e, "event");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r >= 2) times[r - 2] = ms;  // two warm-up runs
+      }
+      if (s != PM_OK) break;
+      std::sort(times, times + 5);
+      if (times[2] < best_ms) {
+        best_ms = times[2];
+        best = t;
+      }
+    }
+    plan->tune = (s == PM_OK) ? best : saved;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(a);
+  cudaFree(b);
+  cudaFree(c);
+  if (s != PM_OK) return s;
+  if (best_out) *best_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
   return ok();
 }
 

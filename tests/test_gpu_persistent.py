@@ -90,3 +90,16 @@ def test_graph_replay(oracle, log2n, variant):
         plan.sync()
         assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis)), rep
     g.close()
+
+
+@pytest.mark.parametrize("log2n,L,P", [(12, 2, 4), (14, 2, 8), (16, 4, 8)])
+def test_autotune_picks_a_valid_choice(oracle, log2n, L, P):
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis, a, b = _setup(log2n, L, P, 14000 + log2n)
+    t, ms = capi.pm_plan_autotune(plan.handle, P)
+    assert ms > 0 and t.variant in (0, 1)
+    got = capi.pm_plan_get_tuning(plan.handle)
+    assert (got.variant, got.row_ops, got.lag_fwd) == (t.variant, t.row_ops, t.lag_fwd)
+    out = to_host(plan.polymul(to_dev(a), to_dev(b)))
+    plan.sync()
+    assert np.array_equal(out, oracle_polymul_batch(oracle, a, b, qs, psis))
