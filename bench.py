@@ -486,6 +486,31 @@ def run_workload(args):
                       "one_launch_tmulmod_per_s": mm / (float(np.median(t1)) * 1e-3) / 1e12})
     elif args.workload == "c5":
         lines.append(run_serving(args, dev))
+    elif args.workload == "reductions":
+        for bits in (30, 60, 62):
+            q = capi.pm_find_params(12, 1, bits)[0][0]
+            r = capi.pm_reduction_rates(dev, q)
+            lines.append({"workload": f"reduction study, {bits}-bit q", "q": q,
+                          "unit": "G reductions/s (register-resident)",
+                          **{k: round(v / 1e9, 1) for k, v in r.items()}})
+    elif args.workload == "tom":
+        # batched stand-alone NTTs: 2^15 transforms of 2^16 points (16 GiB)
+        log2n, count = 16, args.tom_count
+        n = 1 << log2n
+        qs, psis = capi.pm_find_params(log2n, 1, 60)
+        plan = Plan(n, qs, psis)
+        X = inputs.uniform_limbs_torch(inputs.seed_for(5), qs, count, n, device=dev)
+        res = {"workload": f"batched stand-alone NTT: {count} transforms of 2^{log2n} points, 60-bit q",
+               "gib": count * n * 8 / 2**30}
+        for name, fn in [("ntt_fwd", lambda: plan.ntt_fwd_(X, stream=st)),
+                         ("ntt_inv", lambda: plan.ntt_inv_(X, stream=st))]:
+            fn()
+            t = _time_each(fn, 3, st)
+            ms = float(np.median(t))
+            res[name + "_ms"] = ms
+            res[name + "_us_per_ntt"] = ms * 1e3 / count
+            res[name + "_tmulmod_per_s"] = count * (n // 2) * log2n / (ms * 1e-3) / 1e12
+        lines.append(res)
     for line in lines:
         print(json.dumps(line), flush=True)
     return 0
@@ -575,7 +600,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "c1", "c2sweep", "c3", "c4", "c5"])
+                    choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom"])
+    ap.add_argument("--tom-count", type=int, default=1 << 15)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-budget-gb", type=int, default=40)

@@ -340,6 +340,30 @@ pm_status pm_last_error_string(char *buf, size_t n);
  * microbenchmarks of one reduction per operation). */
 pm_status pm_measure_peaks(int device, double *mulmod_per_s, double *imad_per_s);
 
+/* ---- Modular-reduction study (Sec. II-B, Fig. 4) on this GPU.
+ * Variants of reducing a*b mod q for a, b < q, q odd, 4 < q < 2^62:
+ *   PM_RED_BUILTIN    the C '%' operator on the 128-bit product
+ *   PM_RED_ALG2       classical Barrett, Algorithm 2 (up to two corrections)
+ *   PM_RED_ALG3       Dhem-Quisquater, Algorithm 3 (needs len(q) <= 60)
+ *   PM_RED_ALG4       the paper's Barrett variant, Algorithm 4
+ *   PM_RED_SHOUP      Shoup's product (b a constant with a precomputed
+ *                     companion), fully reduced
+ *   PM_RED_MONTGOMERY Montgomery REDC with R = 2^64 (b in Montgomery form) */
+enum {
+    PM_RED_BUILTIN = 0, PM_RED_ALG2 = 1, PM_RED_ALG3 = 2, PM_RED_ALG4 = 3,
+    PM_RED_SHOUP = 4, PM_RED_MONTGOMERY = 5, PM_RED_COUNT = 6
+};
+
+/* Register-resident throughput of each variant (reductions/s) for modulus q;
+ * rates[PM_RED_ALG3] = 0 when len(q) > 60.  Runs short kernels, synchronous. */
+pm_status pm_reduction_rates(int device, uint64_t q, double *rates);
+
+/* d_c[i] = a[i] * b[i] mod q computed with `variant`, n elements on the
+ * current device (for checking each variant; the constants a variant needs
+ * are derived per element). */
+pm_status pm_reduction_apply(int variant, uint64_t q, const uint64_t *d_a, const uint64_t *d_b,
+                             uint64_t *d_c, uint64_t n, void *stream);
+
 /* Library version string. */
 const char *pm_version(void);
 

@@ -53,6 +53,8 @@ SIGNATURES = {
     "pm_graph_create_polymul": (_i32, [ctypes.POINTER(_vp), _vp, _vp, _vp, _vp, _u32]),
     "pm_graph_launch": (_i32, [_vp, _vp]),
     "pm_graph_destroy": (_i32, [_vp]),
+    "pm_reduction_rates": (_i32, [_i32, _u64, ctypes.POINTER(ctypes.c_double)]),
+    "pm_reduction_apply": (_i32, [_i32, _u64, _vp, _vp, _vp, _u64, _vp]),
     "pm_server_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.c_void_p]),
     "pm_server_destroy": (_i32, [_vp]),
     "pm_server_submit": (_i32, [_vp, _vp, _vp, _vp, _u32, ctypes.POINTER(ctypes.c_uint64)]),
@@ -298,6 +300,21 @@ def pm_polymul_uneven(q: int, jobs, stream: int = 0) -> None:
 
 def pm_queue_sync(q: int, stream: int = 0) -> None:
     _call("pm_queue_sync", q, stream)
+
+
+REDUCTIONS = ["builtin %", "alg2 (classical Barrett)", "alg3 (Dhem-Quisquater)",
+              "alg4 (paper's Barrett)", "shoup (constant operand)", "montgomery"]
+
+
+def pm_reduction_rates(device: int, q: int) -> dict:
+    r = (ctypes.c_double * 6)()
+    _call("pm_reduction_rates", device, q, r)
+    return {name: r[i] for i, name in enumerate(REDUCTIONS)}
+
+
+def pm_reduction_apply(variant: int, q: int, d_a: int, d_b: int, d_c: int, n: int,
+                       stream: int = 0) -> None:
+    _call("pm_reduction_apply", variant, q, d_a, d_b, d_c, n, stream)
 
 
 class PmServerConfig(ctypes.Structure):
