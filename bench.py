@@ -204,7 +204,7 @@ def run_gpu(args):
     npoly = max(1, args.batch // L)
     units = npoly * L
     qs, psis = capi.pm_find_params(log2n, L, 60)
-    plan = Plan(n, qs, psis, device=dev)
+    plan = Plan(n, qs, psis, device=dev, fused=args.fused)
     stream = torch.cuda.Stream(device=dev)
     plan.reserve(npoly, stream=stream)
 
@@ -308,6 +308,7 @@ def run_gpu(args):
                    "operand_bytes_per_step": units * n * 8 * 3,
                    "l2": "inputs (%.2f GiB) larger than L2, no flush" % (units * n * 16 / 2**30),
                    "parallelism": f"replicas x{ws}",
+                   "algorithm": "Alg. 8 fused" if args.fused else "Eq. 2 (Alg. 6 / 4 / 7)",
                    "launch": tuning.as_dict()},
         "gpu_launches": (3 if (log2n >= 14 and not persistent) else 1) * args.steps,
         "phase_ms": {"col_fwd": avg_phase[0], "rows": avg_phase[1], "col_inv": avg_phase[2]}
@@ -511,6 +512,33 @@ def run_workload(args):
             res[name + "_us_per_ntt"] = ms * 1e3 / count
             res[name + "_tmulmod_per_s"] = count * (n // 2) * log2n / (ms * 1e-3) / 1e12
         lines.append(res)
+    elif args.workload == "fused":
+        # Eq. 2 vs Algorithm 8 products, batched (~1 GiB of operands per
+        # step) for N = 2^12 .. 2^17; the two plans alternate step by step
+        for log2n in range(12, 18):
+            n = 1 << log2n
+            qs, psis = capi.pm_find_params(log2n, 1, 60)
+            plans = {"eq2": Plan(n, qs, psis), "alg8": Plan(n, qs, psis, fused=True)}
+            P = max(1, (1 << 26) // n)
+            A = inputs.uniform_limbs_torch(log2n, qs, P, n, device=dev)
+            B = inputs.uniform_limbs_torch(log2n + 100, qs, P, n, device=dev)
+            C = torch.empty_like(A)
+            res = {"workload": f"Eq. 2 vs Alg. 8 products, N=2^{log2n}, {P} per step", "N": n,
+                   "products": P}
+            times = {k: [] for k in plans}
+            for p in plans.values():
+                p.reserve(P, stream=st)
+                for _ in range(args.warmup):
+                    p.polymul(A, B, out=C, stream=st)
+            for _ in range(10):
+                for k, p in plans.items():
+                    times[k] += _time_each(lambda: p.polymul(A, B, out=C, stream=st), 1, st)
+            for k in plans:
+                ms = float(np.median(times[k]))
+                res[k + "_ms"] = ms
+                res[k + "_polymuls_per_s"] = P / (ms * 1e-3)
+            res["alg8_speedup"] = res["eq2_ms"] / res["alg8_ms"]
+            lines.append(res)
     for line in lines:
         print(json.dumps(line), flush=True)
     return 0
@@ -600,7 +628,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom"])
+                    choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom",
+                             "fused"])
+    ap.add_argument("--fused", action="store_true",
+                    help="headline products by Algorithm 8 (PM_PLAN_FUSED)")
     ap.add_argument("--tom-count", type=int, default=1 << 15)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)

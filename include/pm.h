@@ -101,11 +101,22 @@ enum {
      * unscaled and 1/N is folded into the last inverse stage (its sum output
      * times N^-1, its twiddle times N^-1).  Both give identical results; the
      * default is faster on this GPU. */
-    PM_PLAN_HALVING = 1
+    PM_PLAN_HALVING = 1,
+    /* Products by the fused polynomial multiplication of Sec. III-C,
+     * Algorithm 8: both forward transforms stop before their last stage
+     * (Algorithm 6 with m < N/2), each pair of bit-reversed positions
+     * (2i, 2i+1) is combined by the Karatsuba step of Algorithm 8 (three
+     * Algorithm 4 products and one product by Psi_br[N/4 + floor(i/2)]),
+     * and the inverse transform starts at its second stage.  Results are
+     * identical to the default (the product is unique); only pm_polymul and
+     * the calls built on it (graphs, uneven batches, serving, host pipeline)
+     * change; pm_ntt_fwd / pm_ntt_inv / pm_pointwise stay full transforms.
+     * Needs N >= 4 (log2n >= 2): pm_plan_create_ex gives PM_ERR_N for N = 2. */
+    PM_PLAN_FUSED = 2
 };
 
 /* pm_plan_create with options: `flags` is a combination of PM_PLAN_*;
- * unknown bits give PM_ERR_ARG. */
+ * unknown bits give PM_ERR_ARG; PM_PLAN_FUSED with log2n < 2 gives PM_ERR_N. */
 pm_status pm_plan_create_ex(pm_plan **out, uint32_t log2n, uint32_t nlimbs,
                             const uint64_t *q, const uint64_t *psi, int device,
                             uint32_t flags);
@@ -213,7 +224,8 @@ pm_status pm_queue_reserve(pm_queue *q, uint64_t units, uint64_t scratch_words);
  * counter (all column-forward tasks first, then rows, then column-inverse
  * tasks), waiting (bounded) on per-unit counters.  Jobs with N <= 2048 run
  * through their plan's own kernel on the same stream.  All plans must be on
- * the queue's device and agree on PM_PLAN_HALVING.  Calls on one queue must
+ * the queue's device and agree on PM_PLAN_HALVING and on PM_PLAN_FUSED
+ * (PM_ERR_ARG otherwise; jobs with N <= 2048 are exempt).  Calls on one queue must
  * be serialised on one stream (they share its buffers). */
 pm_status pm_polymul_uneven(pm_queue *q, const pm_job *jobs, uint32_t njobs, void *stream);
 
@@ -227,7 +239,9 @@ pm_status pm_queue_sync(pm_queue *q, void *stream);
  * admitting a request only when its output (npoly * nlimbs * N words) and
  * column-stage scratch (as many words again for N >= 2^13 unless a == b)
  * fit in the remaining budget of a device arena allocated once at creation,
- * and runs each batch as one uneven persistent launch.  Up to max_inflight
+ * and runs each batch as one uneven persistent launch (a batch holds plans
+ * of one kind -- the same PM_PLAN_HALVING and PM_PLAN_FUSED bits; the first
+ * request of another kind closes it).  Up to max_inflight
  * batches are on the device at once (one stream each), so requests arriving
  * while others run are admitted as soon as a slot and memory free up.
  * A request's output stays in the arena until pm_server_release(). */

@@ -42,14 +42,16 @@ def _stream_handle(stream) -> int:
 class Plan:
     """A device-resident plan for one (N, {q_l}, {psi_l})."""
 
-    def __init__(self, n: int, qs, psis=None, device: int = 0, halving: bool = False):
+    def __init__(self, n: int, qs, psis=None, device: int = 0, halving: bool = False,
+                 fused: bool = False):
         """halving=True scales by 1/2 at every inverse butterfly (the paper's
-        Eq. 2 form); the default folds 1/N into the last inverse stage."""
+        Eq. 2 form); the default folds 1/N into the last inverse stage.
+        fused=True computes products by Algorithm 8 (N >= 4)."""
         self.n = n
         self.log2n = _log2(n)
         self.device = device
-        self._h = capi.pm_plan_create_ex(self.log2n, list(qs), psis, device,
-                                         capi.PM_PLAN_HALVING if halving else 0)
+        flags = (capi.PM_PLAN_HALVING if halving else 0) | (capi.PM_PLAN_FUSED if fused else 0)
+        self._h = capi.pm_plan_create_ex(self.log2n, list(qs), psis, device, flags)
         _, self.nlimbs, self.qs, self.psis = capi.pm_plan_info(self._h)
 
     # -- lifetime

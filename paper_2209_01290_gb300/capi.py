@@ -122,6 +122,7 @@ def pm_find_params(log2n: int, nlimbs: int, qbits: int = 60):
 
 
 PM_PLAN_HALVING = 1
+PM_PLAN_FUSED = 2
 
 
 def pm_plan_create(log2n: int, qs, psis=None, device: int = 0) -> int:

@@ -129,6 +129,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.nunits = npoly * p->nlimbs;
   P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
   P.row_ops = p->tune.row_ops == 2 ? 2 : 1;
+  P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
   return P;
 }
 
@@ -292,9 +293,12 @@ pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const u
 pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const uint64_t* q,
                             const uint64_t* psi, int device, uint32_t flags) {
   if (!out) return fail(PM_ERR_ARG, "out is NULL");
-  if (flags & ~(uint32_t)PM_PLAN_HALVING) return fail(PM_ERR_ARG, "unknown plan flags 0x%x", flags);
+  if (flags & ~(uint32_t)(PM_PLAN_HALVING | PM_PLAN_FUSED))
+    return fail(PM_ERR_ARG, "unknown plan flags 0x%x", flags);
   *out = nullptr;
   if (log2n < 1 || log2n > kMaxLog2N) return fail(PM_ERR_N, "log2n=%u outside [1,17]", log2n);
+  if ((flags & PM_PLAN_FUSED) && log2n < 2)
+    return fail(PM_ERR_N, "PM_PLAN_FUSED needs N >= 4 (Algorithm 8)");
   if (nlimbs < 1 || nlimbs > kMaxLimbs) return fail(PM_ERR_ARG, "nlimbs=%u outside [1,1024]", nlimbs);
   if (!q) return fail(PM_ERR_ARG, "q is NULL");
   const uint64_t n = (uint64_t)1 << log2n;
@@ -349,20 +353,24 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
     destroy_plan(p);
     return cuda_fail(e, "kernel attributes");
   }
-  std::vector<pm::LimbConst> lc(nlimbs);
+  // limb constants: [0, L) plain; for PM_PLAN_FUSED, [L, 2L) the constants
+  // of Algorithm 8's truncated inverse (2/N in place of 1/N)
+  const uint32_t nlc = (flags & PM_PLAN_FUSED) ? 2 * nlimbs : nlimbs;
+  std::vector<pm::LimbConst> lc(nlc);
   std::vector<pm::TwPair> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
   for (uint32_t l = 0; l < nlimbs; ++l)
     pm::host::build_limb(log2n, q[l], psis[l], (flags & PM_PLAN_HALVING) != 0, &lc[l],
                          &twf[(size_t)l * n], &twi[(size_t)l * n]);
+  for (uint32_t l = nlimbs; l < nlc; ++l) pm::host::fused_limb(lc[l - nlimbs], &lc[l]);
   const size_t tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair);
-  if ((e = cudaMalloc(&p->d_lc, nlimbs * sizeof(pm::LimbConst))) != cudaSuccess ||
+  if ((e = cudaMalloc(&p->d_lc, nlc * sizeof(pm::LimbConst))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_twf, tw_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_twi, tw_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&p->d_flag, sizeof(int))) != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "cudaMalloc(plan tables)");
   }
-  if ((e = cudaMemcpy(p->d_lc, lc.data(), nlimbs * sizeof(pm::LimbConst), cudaMemcpyHostToDevice)) !=
+  if ((e = cudaMemcpy(p->d_lc, lc.data(), nlc * sizeof(pm::LimbConst), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
       (e = cudaMemcpy(p->d_twf, twf.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_twi, twi.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
@@ -852,7 +860,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   if (!jobs) return fail(PM_ERR_ARG, "jobs is NULL");
   // validate and size
   uint64_t units = 0, scratch = 0;
-  int halving = -1;
+  int halving = -1, fused = -1;
   for (uint32_t j = 0; j < njobs; ++j) {
     const pm_job& J = jobs[j];
     if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
@@ -866,6 +874,10 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     if (halving >= 0 && h != halving)
       return fail(PM_ERR_ARG, "jobs mix PM_PLAN_HALVING and default plans");
     halving = h;
+    const int f = (J.plan->flags & PM_PLAN_FUSED) ? 1 : 0;
+    if (fused >= 0 && f != fused)
+      return fail(PM_ERR_ARG, "jobs mix PM_PLAN_FUSED and default plans");
+    fused = f;
     const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
     units += u;
     if (J.plan->logn > 12 && J.a != J.b && !(ext_scratch && ext_scratch[j]))
@@ -921,7 +933,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       }
       D.twf = p->d_twf + ((size_t)limb << p->logn);
       D.twi = p->d_twi + ((size_t)limb << p->logn);
-      D.lc = p->d_lc + limb;
+      D.lc = p->d_lc + limb + ((p->flags & PM_PLAN_FUSED) ? p->nlimbs : 0);
       D.logn = p->logn;
       D.pad = 0;
       pf[u] = tf;
@@ -950,7 +962,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   A.tf = tf;
   A.tw = tw;
   A.ti = ti;
-  if ((e = pm::launch_uneven(A, halving == 1, q->num_sms * 3, st)) != cudaSuccess)
+  if ((e = pm::launch_uneven(A, halving == 1, fused == 1, q->num_sms * 3, st)) != cudaSuccess)
     return cuda_fail(e, "uneven launch");
   return ok();
 }
@@ -1289,9 +1301,17 @@ void server_loop(pm_server* S) {
       std::vector<pm_job> jobs;
       std::vector<uint64_t*> scr;
       std::vector<uint64_t> ids;
+      // one uneven launch serves plans of one kind (PM_PLAN_HALVING and
+      // PM_PLAN_FUSED agree); a request of another kind starts the next batch
+      uint32_t kind = ~0u;
       while (!S->queued.empty() && (!S->cfg.max_batch || ids.size() < S->cfg.max_batch)) {
         const uint64_t id = S->queued.front();
         Request& r = S->reqs[id];
+        if (r.plan->logn >= 12) {
+          const uint32_t k = r.plan->flags & (PM_PLAN_HALVING | PM_PLAN_FUSED);
+          if (kind != ~0u && k != kind) break;
+          kind = k;
+        }
         const bool square = r.a == r.b;
         const uint64_t cb = (uint64_t)r.npoly * r.plan->nlimbs << r.plan->logn << 3;
         const uint64_t sb = request_scratch_bytes(r.plan, r.npoly, square);

@@ -7,7 +7,9 @@
 
 namespace pm {
 
-enum Mode { MODE_POLYMUL = 0, MODE_FWD = 1, MODE_INV = 2 };
+// MODE_POLYMUL_FUSED: polymul by Algorithm 8 (truncated transforms around the
+// Karatsuba pair step) instead of Eq. 2's full transforms.
+enum Mode { MODE_POLYMUL = 0, MODE_FWD = 1, MODE_INV = 2, MODE_POLYMUL_FUSED = 3 };
 
 // Kernel parameters for one batched call on one plan.
 struct KParams {
@@ -23,7 +25,8 @@ struct KParams {
   uint32_t nunits;       // npoly * nlimbs
   uint32_t halving;      // 1: per-stage 1/2 scaling (table holds w/2); 0: 1/N folded at the end
   uint32_t row_ops;      // polymul row kernel: 1 = operands one after the other, 2 = together
-  uint32_t pad;
+  uint32_t fused;        // polymul by Algorithm 8; lc then has 2 nlimbs entries, the second
+                         // half (2/N in place of 1/N) used by the polymul launchers
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the
@@ -51,7 +54,7 @@ struct alignas(64) UnitDesc {
   uint64_t* s;           // scratch N words for b's image (== c for a square)
   const TwPair* twf;     // the unit's limb tables (its plan)
   const TwPair* twi;
-  const LimbConst* lc;
+  const LimbConst* lc;    // the fused constants for an Algorithm 8 plan
   uint32_t logn;
   uint32_t pad;
 };
@@ -67,7 +70,8 @@ struct UnevenArgs {
 };
 
 cudaError_t uneven_prepare();
-cudaError_t launch_uneven(const UnevenArgs& A, bool halving, int grid, cudaStream_t st);
+cudaError_t launch_uneven(const UnevenArgs& A, bool halving, bool fused, int grid,
+                          cudaStream_t st);
 
 cudaError_t persist_prepare();
 size_t persist_ctl_words(uint32_t nunits);

@@ -80,13 +80,14 @@ __global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
   } else {
     (void)sb;
     row_task_polymul<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
-                                   P.c + off, single, smem, twf, twi, K, logn, t);
+                                   P.c + off, single, smem, twf, twi, K, logn, t,
+                                   MODE == MODE_POLYMUL_FUSED);
   }
 }
 
 // Polymul rows with a and b transformed together in registers (shared
 // twiddle loads, half the barriers per word; 2 CTAs per SM).
-template <bool HALVE>
+template <bool HALVE, bool FUSED>
 __global__ void __launch_bounds__(256, 2) k_rows2(KParams P) {
   extern __shared__ __align__(16) uint64_t smem[];
   const uint32_t logn = P.logn;
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(256, 2) k_rows2(KParams P) {
   const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
   const bool single = (logn == kRowLog);
   row_task_polymul2<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
-                                  P.c + off, single, smem, twf, twi, K, logn, t);
+                                  P.c + off, single, smem, twf, twi, K, logn, t, FUSED);
 }
 
 // Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
@@ -223,8 +224,9 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
   uint64_t* sb = sB + rho * kRowPad;
   const size_t base = (size_t)unit << logn;
   uint64_t v[16];
-  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
-    const int nops = (MODE == MODE_POLYMUL) ? 2 : 1;
+  constexpr bool kFused = (MODE == MODE_POLYMUL_FUSED);
+  if constexpr (MODE != MODE_INV) {
+    const int nops = (MODE == MODE_FWD) ? 1 : 2;
     const TwPair w = ld_tw(twf + 1);
     for (int op = 0; op < nops; op++) {
       const uint64_t* src = (MODE == MODE_FWD) ? P.c + base : (op == 0 ? P.a : P.b) + base;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       }
     }
     __syncthreads();
-    rows_fwd(v, nullptr, sa, twf, logn, rho, th, K.q, K.two_q);
+    rows_fwd(v, nullptr, sa, twf, logn, rho, th, K.q, K.two_q, kFused);
     if constexpr (MODE == MODE_FWD) {
       ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + base + (size_t)rho * kRow + 16 * th);
 #pragma unroll
@@ -250,11 +252,14 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
     } else {
       const PassGeo G2 = pass_geo(2, th, rho);
       st_smem16(sa, G2, v);
-      rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q);
+      rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q, kFused);
+      const uint64_t* a2 = sa + G2.pbase;
+      if constexpr (kFused) {
+        fused_pairs16(v, a2, twf, logn, G2.g, K);
+      } else {
 #pragma unroll
-      for (int u = 0; u < 16; u++) {
-        const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
-        v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
+        for (int u = 0; u < 16; u++)
+          v[u] = mul_barrett_alg4(reduce4(a2[u], K.q, K.two_q), reduce4(v[u], K.q, K.two_q), K);
       }
     }
   } else {
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       v[u + 1] = w.y;
     }
   }
-  rows_inv<HALVE>(v, nullptr, false, sa, twi, logn, rho, th, K);
+  rows_inv<HALVE>(v, nullptr, false, sa, twi, logn, rho, th, K, kFused);
   __syncthreads();
   // last GS stage (k = 4096, twiddle Psi^-1_br[1]; 1/N folded in unless the
   // plan halves at every stage), then reduce
@@ -301,14 +306,18 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
   uint64_t* xa = smem;
   uint64_t* xb = smem + n;
   const uint64_t q = K.q, two_q = K.two_q;
-  if constexpr (MODE == MODE_FWD || MODE == MODE_POLYMUL) {
-    const int nops = (MODE == MODE_POLYMUL) ? 2 : 1;
+  // Algorithm 8 (n >= 4): CT stops before its last stage (m = n/2), the pair
+  // step replaces that stage, the products and the first GS stage, and GS
+  // starts at m = n/4.
+  constexpr bool kFused = (MODE == MODE_POLYMUL_FUSED);
+  if constexpr (MODE != MODE_INV) {
+    const int nops = (MODE == MODE_FWD) ? 1 : 2;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
       xa[i] = (MODE == MODE_FWD) ? P.c[base + i] : P.a[base + i];
       if (nops == 2) xb[i] = P.b[base + i];
     }
     __syncthreads();
-    for (uint32_t m = 1, k = n >> 1; m < n; m <<= 1, k >>= 1) {
+    for (uint32_t m = 1, k = n >> 1; m < (kFused ? n >> 1 : n); m <<= 1, k >>= 1) {
       for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
         const uint32_t i = b / k, j = 2 * i * k + (b % k);
         const TwPair w = ld_tw(twf + m + i);
@@ -321,13 +330,23 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
       for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P.c[base + i] = reduce4(xa[i], q, two_q);
       return;
     }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
-      xa[i] = mul_barrett_alg4(reduce4(xa[i], q, two_q), reduce4(xb[i], q, two_q), K);
+    if constexpr (kFused) {
+      for (uint32_t i = threadIdx.x; i < n / 2; i += blockDim.x) {
+        const TwPair w = ld_tw(twf + n / 4 + i / 2);
+        if (i & 1)
+          fused_pair<true>(xa[2 * i], xa[2 * i + 1], xb[2 * i], xb[2 * i + 1], w, K);
+        else
+          fused_pair<false>(xa[2 * i], xa[2 * i + 1], xb[2 * i], xb[2 * i + 1], w, K);
+      }
+    } else {
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+        xa[i] = mul_barrett_alg4(reduce4(xa[i], q, two_q), reduce4(xb[i], q, two_q), K);
+    }
   } else {
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) xa[i] = P.c[base + i];
   }
   __syncthreads();
-  for (uint32_t m = n >> 1, k = 1; m >= 1; m >>= 1, k <<= 1) {
+  for (uint32_t m = n >> (kFused ? 2 : 1), k = kFused ? 2 : 1; m >= 1; m >>= 1, k <<= 1) {
     for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
       const uint32_t i = b / k, j = 2 * i * k + (b % k);
       if (!HALVE && m == 1) {
@@ -446,11 +465,12 @@ constexpr int kFused13Smem = 4 * kRowPad * 8;
 template <int MODE>
 static cudaError_t rows(const KParams& P, cudaStream_t st) {
   const unsigned blocks = P.nunits << (P.logn - kRowLog);
-  if (MODE == MODE_POLYMUL && P.row_ops == 2) {
+  if ((MODE == MODE_POLYMUL || MODE == MODE_POLYMUL_FUSED) && P.row_ops == 2) {
+    constexpr bool F = (MODE == MODE_POLYMUL_FUSED);
     if (P.halving)
-      k_rows2<true><<<blocks, 256, kRowsSmem, st>>>(P);
+      k_rows2<true, F><<<blocks, 256, kRowsSmem, st>>>(P);
     else
-      k_rows2<false><<<blocks, 256, kRowsSmem, st>>>(P);
+      k_rows2<false, F><<<blocks, 256, kRowsSmem, st>>>(P);
     return cudaGetLastError();
   }
   if (P.halving)
@@ -483,10 +503,14 @@ template <bool H>
 static cudaError_t prepare_mode() {
   cudaError_t e;
   if ((e = set_smem((const void*)k_rows<MODE_POLYMUL, H>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows2<H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL_FUSED, H>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows2<H, false>, kRowsSmem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_rows2<H, true>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_rows<MODE_FWD, H>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_rows<MODE_INV, H>, kRowsSmem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL, H>, kFused13Smem)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL_FUSED, H>, kFused13Smem)) != cudaSuccess)
+    return e;
   if ((e = set_smem((const void*)k_fused13<MODE_FWD, H>, kFused13Smem)) != cudaSuccess) return e;
   if ((e = set_smem((const void*)k_fused13<MODE_INV, H>, kFused13Smem)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -503,14 +527,26 @@ static inline cudaError_t mark(const PhaseEvents* pe, int k, cudaStream_t st) {
   return (pe && k < pe->n) ? cudaEventRecord(pe->ev[k], st) : cudaSuccess;
 }
 
+template <int MODE>
+static cudaError_t polymul_rows(const KParams& P, cudaStream_t st) {
+  if (P.logn <= 11) return small<MODE>(P, st);
+  if (P.logn == 12) return rows<MODE>(P, st);
+  if (P.logn == 13) return fused13<MODE>(P, st);
+  return rows<MODE>(P, st);
+}
+
 cudaError_t launch_polymul(const KParams& P0, cudaStream_t st, const PhaseEvents* pe) {
   KParams P = P0;
   if (P.nunits == 0) return cudaSuccess;
+  // Algorithm 8 plans: the fused constants (2/N) follow the plain ones
+  if (P.fused) P.lc += P.nlimbs;
+  auto prows = [&](const KParams& Q) {
+    return Q.fused ? polymul_rows<MODE_POLYMUL_FUSED>(Q, st) : polymul_rows<MODE_POLYMUL>(Q, st);
+  };
   cudaError_t e0 = mark(pe, 0, st);
   if (e0 != cudaSuccess) return e0;
   if (P.logn <= 13) {
-    e0 = P.logn <= 11 ? small<MODE_POLYMUL>(P, st)
-                      : (P.logn == 12 ? rows<MODE_POLYMUL>(P, st) : fused13<MODE_POLYMUL>(P, st));
+    e0 = prows(P);
     if (e0 != cudaSuccess) return e0;
     return mark(pe, 1, st);
   }
@@ -530,7 +566,7 @@ cudaError_t launch_polymul(const KParams& P0, cudaStream_t st, const PhaseEvents
   }
   cudaError_t e = col_fwd(P, nops, st);
   if (e == cudaSuccess) e = mark(pe, 1, st);
-  if (e == cudaSuccess) e = rows<MODE_POLYMUL>(P, st);
+  if (e == cudaSuccess) e = prows(P);
   if (e == cudaSuccess) e = mark(pe, 2, st);
   if (e == cudaSuccess) e = col_inv(P, st);
   if (e == cudaSuccess) e = mark(pe, 3, st);

@@ -152,5 +152,14 @@ void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbCons
   lc->w1ninv_p = shoup_companion(lc->w1ninv, q);
 }
 
+void fused_limb(const LimbConst& in, LimbConst* out) {
+  *out = in;
+  const uint64_t q = in.q;
+  out->ninv = mul_mod(in.ninv, 2, q);
+  out->ninv_p = shoup_companion(out->ninv, q);
+  out->w1ninv = mul_mod(in.w1ninv, 2, q);
+  out->w1ninv_p = shoup_companion(out->w1ninv, q);
+}
+
 }  // namespace host
 }  // namespace pm

@@ -20,6 +20,10 @@ uint64_t default_psi(uint64_t q, uint32_t log2n);
 // Sec. III-A); otherwise Psi^-1_br[i] and 1/N is folded into the last stage.
 void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbConst* lc,
                 TwPair* twf, TwPair* twi);
+// Constants for the fused polynomial multiplication (Algorithm 8): its pair
+// step already carries the 1/2 of the omitted first GS stage, so the scale
+// folded into the last stage becomes 2/N (N^-1 and Psi^-1_br[1] N^-1 times 2).
+void fused_limb(const LimbConst& in, LimbConst* out);
 
 }  // namespace host
 }  // namespace pm

@@ -60,21 +60,24 @@ __device__ __forceinline__ void ct16_stage2(uint64_t (&va)[16], uint64_t (&vb)[1
   }
 }
 
+// skip_last omits the fourth stage: in the last pass of a forward transform
+// that is the transform's final stage, which Algorithm 8 leaves out.
 __device__ __forceinline__ void ct16_2(uint64_t (&va)[16], uint64_t (&vb)[16],
                                        const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
-                                       uint64_t q, uint64_t two_q) {
+                                       uint64_t q, uint64_t two_q, bool skip_last = false) {
   ct16_stage2<0>(va, vb, tw, s0, g, q, two_q);
   ct16_stage2<1>(va, vb, tw, s0, g, q, two_q);
   ct16_stage2<2>(va, vb, tw, s0, g, q, two_q);
-  ct16_stage2<3>(va, vb, tw, s0, g, q, two_q);
+  if (!skip_last) ct16_stage2<3>(va, vb, tw, s0, g, q, two_q);
 }
 
 __device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                     uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
+                                     uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q,
+                                     bool skip_last = false) {
   ct16_stage1<0>(v, tw, s0, g, q, two_q);
   ct16_stage1<1>(v, tw, s0, g, q, two_q);
   ct16_stage1<2>(v, tw, s0, g, q, two_q);
-  ct16_stage1<3>(v, tw, s0, g, q, two_q);
+  if (!skip_last) ct16_stage1<3>(v, tw, s0, g, q, two_q);
 }
 
 // Four consecutive merged-GS stages (Algorithm 7, 1/2-scaled) on a group of
@@ -96,11 +99,14 @@ __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __re
   }
 }
 
+// skip_first omits the first stage (the transform's first when sig0 = 0,
+// which Algorithm 8 leaves out).
 template <bool HALVE>
 __device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                      uint32_t logn, uint32_t sig0, uint32_t g,
-                                     uint64_t q, uint64_t two_q, uint64_t hq) {
-  gs16_stage<0, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
+                                     uint64_t q, uint64_t two_q, uint64_t hq,
+                                     bool skip_first = false) {
+  if (!skip_first) gs16_stage<0, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
   gs16_stage<1, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
   gs16_stage<2, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
   gs16_stage<3, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
@@ -264,10 +270,13 @@ __device__ __forceinline__ uint64_t ld_g(const uint64_t* p) {
 // Forward in-row stages of one operand.  Source: global row `g_src` (layout
 // 0, coalesced) or, if null, the smem row `s` (already holding the row).
 // Leaves the last pass's 16 words (layout 2, lazy [0,4q)) in v.
+// With `trunc` the transform's final stage is omitted (Algorithm 8's
+// truncated CT transform).
 template <bool CG = false>
 __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_src, uint64_t* s,
                                          const TwPair* __restrict__ twf, uint32_t logn,
-                                         uint32_t t, int th, uint64_t q, uint64_t two_q) {
+                                         uint32_t t, int th, uint64_t q, uint64_t two_q,
+                                         bool trunc = false) {
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
     const PassGeo G = pass_geo(p, th, t);
@@ -277,7 +286,7 @@ __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_sr
     } else {
       ld_smem16(v, s, G);
     }
-    ct16(v, twf, logn - 12 + 4 * p, G.g, q, two_q);
+    ct16(v, twf, logn - 12 + 4 * p, G.g, q, two_q, trunc && p == 2);
     if (p < 2) {
       st_smem16(s, G, v);
       // pass 1 -> 2 stays inside a half-warp: the layout-1 block g of 256
@@ -295,17 +304,20 @@ __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_sr
 // The last pass writes layout 0 either to the global row `g_dst`
 // (canonical if `final`) or, if null, back to smem.
 // With `final` (the row is the whole transform, N = 4096) and no per-stage
-// halving, the outputs are multiplied by N^-1 before the store.
+// halving, the outputs are multiplied by N^-1 (K.ninv) before the store.
+// With `trunc` the transform's first stage is omitted (Algorithm 8's
+// truncated GS transform).
 template <bool HALVE>
 __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, bool final,
                                          uint64_t* s, const TwPair* __restrict__ twi,
-                                         uint32_t logn, uint32_t t, int th, const LimbConst& K) {
+                                         uint32_t logn, uint32_t t, int th, const LimbConst& K,
+                                         bool trunc = false) {
   const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
     const PassGeo G = pass_geo(2 - p, th, t);
     if (p > 0) ld_smem16(v, s, G);
-    gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq);
+    gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq, trunc && p == 0);
     if (p < 2) {
       st_smem16(s, G, v);
       // layout 2 -> 1 stays inside a half-warp, layout 1 -> 0 crosses warps
@@ -335,7 +347,7 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
                                           const uint64_t* ga, const uint64_t* gb, uint64_t* sa,
                                           uint64_t* sb, const TwPair* __restrict__ twf,
                                           uint32_t logn, uint32_t t, int th, uint64_t q,
-                                          uint64_t two_q) {
+                                          uint64_t two_q, bool trunc = false) {
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
     const PassGeo G = pass_geo(p, th, t);
@@ -349,7 +361,7 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
       ld_smem16(va, sa, G);
       ld_smem16(vb, sb, G);
     }
-    ct16_2(va, vb, twf, logn - 12 + 4 * p, G.g, q, two_q);
+    ct16_2(va, vb, twf, logn - 12 + 4 * p, G.g, q, two_q, trunc && p == 2);
     if (p < 2) {
       st_smem16(sa, G, va);
       st_smem16(sb, G, vb);
@@ -361,50 +373,110 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
   }
 }
 
+// Algorithm 8's fused step for one pair of bit-reversed positions (2i, 2i+1):
+// (x0, x1) from the truncated CT transform of a, (y0, y1) from that of b,
+// lazy in [0, 4q).  With gamma = (-1)^i Psi_br[N/4 + floor(i/2)] (the square
+// of the omitted last stage's twiddle Psi_br[N/2 + i]):
+//   x0 <- x0 y0 + gamma x1 y1,   x1 <- x0 y1 + x1 y0 = (x0+x1)(y0+y1) - x0 y0 - x1 y1
+// with three Algorithm 4 products and one Shoup product by Psi_br[..]; the
+// sign (-1)^i is a compile-time choice between u + z and u - z.  This is the
+// first GS stage's output with its 1/2, in [0, 2q).
+template <bool ODD>
+__device__ __forceinline__ void fused_pair(uint64_t& x0, uint64_t& x1, uint64_t y0, uint64_t y1,
+                                           const TwPair& w, const LimbConst& K) {
+  const uint64_t q = K.q, two_q = K.two_q;
+  const uint64_t a0 = reduce4(x0, q, two_q), a1 = reduce4(x1, q, two_q);
+  const uint64_t b0 = reduce4(y0, q, two_q), b1 = reduce4(y1, q, two_q);
+  const uint64_t u = mul_barrett_alg4(a0, b0, K);                               // [0, q)
+  const uint64_t v = mul_barrett_alg4(a1, b1, K);                               // [0, q)
+  const uint64_t w3 = mul_barrett_alg4(csub(a0 + a1, q), csub(b0 + b1, q), K);  // [0, q)
+  const uint64_t z = mul_shoup_lazy(v, w.w, w.wp, q);                           // [0, 2q)
+  x1 = csub(w3 + two_q - u - v, two_q);                                         // (0,3q) -> [0,2q)
+  x0 = csub(ODD ? u + two_q - z : u + z, two_q);                                // [0,3q) -> [0,2q)
+}
+
+// The fused step on the 8 pairs (u, u+1) of a layout-2 register group (group
+// g = 256 t + th holds bit-reversed positions 16 g + u): pair i = 8 g + u/2,
+// so floor(i/2) = 4 g + u/4 and i is odd when u/2 is.  Result in va.  The
+// step is symmetric in the two operands; vb may be a register array or a
+// pointer to the other operand's words (read once each).
+template <typename VB>
+__device__ __forceinline__ void fused_pairs16(uint64_t (&va)[16], const VB& vb,
+                                              const TwPair* __restrict__ twf, uint32_t logn,
+                                              uint32_t g, const LimbConst& K) {
+  const uint32_t base = (1u << (logn - 2)) + 4 * g;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const TwPair w = ld_tw(twf + base + k);
+    fused_pair<false>(va[4 * k], va[4 * k + 1], vb[4 * k], vb[4 * k + 1], w, K);
+    fused_pair<true>(va[4 * k + 2], va[4 * k + 3], vb[4 * k + 2], vb[4 * k + 3], w, K);
+  }
+}
+
+// The product step between the forward and inverse in-row stages: Algorithm
+// 4 pointwise products (Eq. 2) or, with `fused`, Algorithm 8's pair step.
+__device__ __forceinline__ void row_product(uint64_t (&va)[16], const uint64_t (&vb)[16],
+                                            bool fused, const TwPair* __restrict__ twf,
+                                            uint32_t logn, uint32_t g, const LimbConst& K) {
+  if (fused) {
+    fused_pairs16(va, vb, twf, logn, g, K);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; u++)
+      va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
+  }
+}
+
 // Polymul row task with both operands in registers at once (2 CTAs per SM).
 template <bool HALVE, bool CG>
 __device__ __forceinline__ void row_task_polymul2(const uint64_t* ga, const uint64_t* gb,
                                                   uint64_t* gc, bool single, uint64_t* smem,
                                                   const TwPair* __restrict__ twf,
                                                   const TwPair* __restrict__ twi,
-                                                  const LimbConst& K, uint32_t logn, uint32_t t) {
+                                                  const LimbConst& K, uint32_t logn, uint32_t t,
+                                                  bool fused = false) {
   const int th = threadIdx.x;
   uint64_t* sa = smem;
   uint64_t* sb = smem + kRowPad;
   uint64_t va[16], vb[16];
-  rows_fwd2<CG>(va, vb, ga, gb, sa, sb, twf, logn, t, th, K.q, K.two_q);
-#pragma unroll
-  for (int u = 0; u < 16; u++)
-    va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
-  rows_inv<HALVE>(va, gc, single, sa, twi, logn, t, th, K);
+  rows_fwd2<CG>(va, vb, ga, gb, sa, sb, twf, logn, t, th, K.q, K.two_q, fused);
+  row_product(va, vb, fused, twf, logn, pass_geo(2, th, t).g, K);
+  rows_inv<HALVE>(va, gc, single, sa, twi, logn, t, th, K, fused);
 }
 
 // Polymul row task: forward in-row stages of a and b, Algorithm 4 pointwise
 // product, inverse in-row stages, for row t of `unit`.  `ga`, `gb` are the
 // global rows of the operands (the column-transformed images for N > 4096),
 // `gc` the output row.  `smem` holds 2 padded rows.
+// With `fused` the task follows Algorithm 8 (truncated transforms around
+// the pair step); K must then hold the fused constants (2/N).
 template <bool HALVE, bool CG>
 __device__ __forceinline__ void row_task_polymul(const uint64_t* ga, const uint64_t* gb,
                                                  uint64_t* gc, bool single, uint64_t* smem,
                                                  const TwPair* __restrict__ twf,
                                                  const TwPair* __restrict__ twi,
-                                                 const LimbConst& K, uint32_t logn, uint32_t t) {
+                                                 const LimbConst& K, uint32_t logn, uint32_t t,
+                                                 bool fused = false) {
   const int th = threadIdx.x;
   uint64_t* sa = smem;
   uint64_t* sb = smem + kRowPad;
   uint64_t v[16];
   // operand a: keep its transform in smem (layout 2) while b is done
-  rows_fwd<CG>(v, ga, sa, twf, logn, t, th, K.q, K.two_q);
+  rows_fwd<CG>(v, ga, sa, twf, logn, t, th, K.q, K.two_q, fused);
   const PassGeo G2 = pass_geo(2, th, t);
   st_smem16(sa, G2, v);
-  rows_fwd<CG>(v, gb, sb, twf, logn, t, th, K.q, K.two_q);
-  // pointwise product (Algorithm 4) in bit-reversed order
+  rows_fwd<CG>(v, gb, sb, twf, logn, t, th, K.q, K.two_q, fused);
+  // product step in bit-reversed order (Algorithm 4 products, or Algorithm
+  // 8's pair step); each thread re-reads only the words it stored itself
+  const uint64_t* a2 = sa + G2.pbase;
+  if (fused) {
+    fused_pairs16(v, a2, twf, logn, G2.g, K);
+  } else {
 #pragma unroll
-  for (int u = 0; u < 16; u++) {
-    const uint64_t ahat = reduce4(sa[G2.pbase + u], K.q, K.two_q);
-    v[u] = mul_barrett_alg4(ahat, reduce4(v[u], K.q, K.two_q), K);
+    for (int u = 0; u < 16; u++)
+      v[u] = mul_barrett_alg4(reduce4(a2[u], K.q, K.two_q), reduce4(v[u], K.q, K.two_q), K);
   }
-  rows_inv<HALVE>(v, gc, single, sa, twi, logn, t, th, K);
+  rows_inv<HALVE>(v, gc, single, sa, twi, logn, t, th, K, fused);
 }
 
 }  // namespace pm

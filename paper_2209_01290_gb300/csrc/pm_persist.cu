@@ -206,7 +206,7 @@ __device__ void run_task(const KParams& P, const PersistArgs& A, uint32_t ticket
     const size_t off = ((size_t)unit << logn) + (size_t)r * kRow;
     const bool single = (logn == kRowLog);
     row_task_polymul<HALVE, true>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
-                                  P.c + off, single, smem, twf, twi, K, logn, r);
+                                  P.c + off, single, smem, twf, twi, K, logn, r, P.fused != 0);
     if (A.I) cta_signal(done + 2 * unit + 1);
     return;
   }
@@ -283,6 +283,7 @@ cudaError_t launch_polymul_persistent(const KParams& P0, uint32_t* ctl, int grid
   if (P0.nunits == 0) return cudaSuccess;
   if (P0.logn < 12 || P0.logn > 17) return cudaErrorInvalidValue;
   KParams P = P0;
+  if (P.fused) P.lc += P.nlimbs;  // Algorithm 8: the fused constants (2/N)
   int nops = 2;
   if (P.logn > 12) {
     if (P.a == P.b) {
@@ -346,7 +347,7 @@ __device__ __forceinline__ uint32_t find_unit(const uint32_t* __restrict__ pre, 
   return lo;
 }
 
-template <bool HALVE>
+template <bool HALVE, bool FUSED>
 __device__ void run_uneven_task(const UnevenArgs& A, uint32_t ticket, uint64_t* smem) {
   uint32_t* done = A.ctl + 4;
   int* err = reinterpret_cast<int*>(A.ctl + 1);
@@ -389,7 +390,7 @@ __device__ void run_uneven_task(const UnevenArgs& A, uint32_t ticket, uint64_t* 
     const size_t off = (size_t)r * kRow;
     const bool single = (logn == kRowLog);
     row_task_polymul<HALVE, true>((single ? D.a : D.c) + off, (single ? D.b : D.s) + off,
-                                  D.c + off, single, smem, D.twf, D.twi, K, logn, r);
+                                  D.c + off, single, smem, D.twf, D.twi, K, logn, r, FUSED);
     if (!single) cta_signal(done + 2 * unit + 1);
   } else {
     cta_wait(done + 2 * unit + 1, R, err);
@@ -406,7 +407,10 @@ __device__ void run_uneven_task(const UnevenArgs& A, uint32_t ticket, uint64_t* 
 
 }  // namespace
 
-template <bool HALVE>
+// FUSED: every unit's plan has PM_PLAN_FUSED (Algorithm 8 row tasks).  A
+// compile-time choice: with a run-time flag the row task's two product
+// steps raise the kernel's register spills several-fold.
+template <bool HALVE, bool FUSED>
 __global__ void __launch_bounds__(256, 3) k_uneven(UnevenArgs A) {
   extern __shared__ __align__(16) uint64_t smem[];
   __shared__ uint32_t s_ticket;
@@ -417,27 +421,38 @@ __global__ void __launch_bounds__(256, 3) k_uneven(UnevenArgs A) {
     const uint32_t ticket = s_ticket;
     __syncthreads();
     if (ticket >= total) break;
-    run_uneven_task<HALVE>(A, ticket, smem);
+    run_uneven_task<HALVE, FUSED>(A, ticket, smem);
     __syncthreads();
   }
 }
 
 cudaError_t uneven_prepare() {
-  cudaError_t e = cudaFuncSetAttribute((const void*)k_uneven<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute((const void*)k_uneven<true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+  const void* fns[4] = {(const void*)k_uneven<false, false>, (const void*)k_uneven<true, false>,
+                        (const void*)k_uneven<false, true>, (const void*)k_uneven<true, true>};
+  for (const void* f : fns) {
+    cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kPersistSmem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_uneven(const UnevenArgs& A, bool halving, int grid, cudaStream_t st) {
+cudaError_t launch_uneven(const UnevenArgs& A, bool halving, bool fused, int grid,
+                          cudaStream_t st) {
   if (A.nunits == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(A.ctl, 0, (4 + 2 * (size_t)A.nunits) * 4, st);
   if (e != cudaSuccess) return e;
-  if (halving)
-    k_uneven<true><<<grid, 256, kPersistSmem, st>>>(A);
-  else
-    k_uneven<false><<<grid, 256, kPersistSmem, st>>>(A);
+  if (halving) {
+    if (fused)
+      k_uneven<true, true><<<grid, 256, kPersistSmem, st>>>(A);
+    else
+      k_uneven<true, false><<<grid, 256, kPersistSmem, st>>>(A);
+  } else {
+    if (fused)
+      k_uneven<false, true><<<grid, 256, kPersistSmem, st>>>(A);
+    else
+      k_uneven<false, false><<<grid, 256, kPersistSmem, st>>>(A);
+  }
   return cudaGetLastError();
 }
 
