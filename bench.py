@@ -344,11 +344,15 @@ def _flush_l2(buf):
 
 
 def _time_each(fn, reps, stream, flush=None):
+    """Device time of fn() on `stream`, one event pair per call.  The L2
+    flush runs on the same stream, before the start event, so that it is
+    finished (and not competing for HBM) when the timed work starts."""
     import torch
     out = []
     for _ in range(reps):
         if flush is not None:
-            flush()
+            with torch.cuda.stream(stream):
+                flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         fn()

@@ -294,7 +294,7 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  * row_ops (SPLIT only): 1 = the row kernel transforms a then b (3 CTAs per
  * SM), 2 = both together sharing twiddle loads (2 CTAs per SM).
  * pm_plan_autotune() picks these by timing; without it a plan uses SPLIT,
- * row_ops 1 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
+ * row_ops 2 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
 enum { PM_VARIANT_SPLIT = 0, PM_VARIANT_PERSISTENT = 1 };
 typedef struct pm_tuning {
     int32_t variant;

@@ -18,6 +18,15 @@ __device__ __forceinline__ TwPair ld_tw(const TwPair* __restrict__ p) {
   return TwPair{v.x, v.y};
 }
 
+// Two consecutive twiddle pairs p[0], p[1] in one 256-bit read-only load.
+// p must be 32-byte aligned: every caller passes an even index into a table
+// whose base is 32-byte aligned (cudaMalloc'ed, per-limb offsets N * 16 B).
+__device__ __forceinline__ void ld_tw2(const TwPair* __restrict__ p, TwPair& t0, TwPair& t1) {
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(t0.w), "=l"(t0.wp), "=l"(t1.w), "=l"(t1.wp)
+      : "l"(p));
+}
+
 // w * y mod q up to one multiple of q (Shoup): for w < q and any 64-bit y,
 // the result is congruent to w*y and lies in [0, 2q).  Written as
 // w*y + qh*(2^64 - q) mod 2^64 so that the subtraction folds into the

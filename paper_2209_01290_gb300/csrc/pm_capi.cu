@@ -337,7 +337,7 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   p->tune.ctas_per_sm = 3;
   p->tune.lag_fwd = 8;
   p->tune.lag_inv = 64;
-  p->tune.row_ops = 1;
+  p->tune.row_ops = 2;
   p->logn = log2n;
   p->nlimbs = nlimbs;
   p->q.assign(q, q + nlimbs);
@@ -702,8 +702,8 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
   // candidates: the split path with either row kernel, the persistent launch
   // with a few pipeline distances
   std::vector<pm_tuning> cand;
-  cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
-  if (plan->logn >= 14) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
+  cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
+  if (plan->logn >= 12 && plan->logn != 13) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
   if (plan->logn >= 13) {
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});

@@ -254,13 +254,10 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
       st_smem16(sa, G2, v);
       rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q, kFused);
       const uint64_t* a2 = sa + G2.pbase;
-      if constexpr (kFused) {
-        fused_pairs16(v, a2, twf, logn, G2.g, K);
-      } else {
-#pragma unroll
-        for (int u = 0; u < 16; u++)
-          v[u] = mul_barrett_alg4(reduce4(a2[u], K.q, K.two_q), reduce4(v[u], K.q, K.two_q), K);
-      }
+      if constexpr (kFused)
+        fused_pairs16_smem(v, a2, twf, logn, G2.g, K);
+      else
+        pointwise16(v, a2, K);
     }
   } else {
     const ulonglong2* src =

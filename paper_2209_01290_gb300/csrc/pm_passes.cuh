@@ -13,12 +13,15 @@ namespace pm {
 
 constexpr int kRowLog = 12;
 constexpr int kRow = 1 << kRowLog;        // 4096 words per row
-// One pad word after every 16: 64-bit shared accesses are served per
-// half-warp, and with this padding the 16 lanes of a half-warp hit 16
-// different bank pairs in every thread layout used below.
-constexpr int kRowPad = kRow + kRow / 16;
+// Two pad words after every 16 (p(j) = j + 2 floor(j/16)).  64-bit shared
+// accesses are served per half-warp and 128-bit ones per quarter-warp; with
+// this padding layouts 0 and 1 (64-bit, a half-warp reads 16 consecutive
+// words) and layout 2 (128-bit word pairs, quarter-warp chunks 9 th + u/2 are
+// distinct mod 8) are all free of bank conflicts, and every layout-2 pair
+// starts on a 16-byte boundary.
+constexpr int kRowPad = kRow + kRow / 8;
 
-__device__ __forceinline__ int padj(int j) { return j + (j >> 4); }
+__device__ __forceinline__ int padj(int j) { return j + 2 * (j >> 4); }
 
 // ------------------------------------------------------------------ passes
 
@@ -31,13 +34,23 @@ template <int ST>
 __device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __restrict__ tw,
                                             uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
   constexpr int h = 8 >> ST;
-  const uint32_t base = (1u << (s0 + ST)) + (g << ST);
+  const uint32_t base = (1u << (s0 + ST)) + (g << ST);  // even for ST >= 1
+  if constexpr (ST == 0) {
+    const TwPair t = ld_tw(tw + base);
 #pragma unroll
-  for (int blk = 0; blk < (1 << ST); blk++) {
-    const TwPair t = ld_tw(tw + base + blk);
+    for (int u0 = 0; u0 < 8; u0++) ct_bfly(v[u0], v[u0 + 8], t.w, t.wp, q, two_q);
+  } else {
 #pragma unroll
-    for (int u0 = 0; u0 < h; u0++)
-      ct_bfly(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+    for (int blk = 0; blk < (1 << ST); blk += 2) {
+      TwPair t[2];
+      ld_tw2(tw + base + blk, t[0], t[1]);
+#pragma unroll
+      for (int e = 0; e < 2; e++)
+#pragma unroll
+        for (int u0 = 0; u0 < h; u0++)
+          ct_bfly(v[(blk + e) * 2 * h + u0], v[(blk + e) * 2 * h + u0 + h], t[e].w, t[e].wp, q,
+                  two_q);
+    }
   }
 }
 
@@ -48,15 +61,23 @@ __device__ __forceinline__ void ct16_stage2(uint64_t (&va)[16], uint64_t (&vb)[1
                                             const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
                                             uint64_t q, uint64_t two_q) {
   constexpr int h = 8 >> ST;
-  const uint32_t base = (1u << (s0 + ST)) + (g << ST);
+  const uint32_t base = (1u << (s0 + ST)) + (g << ST);  // even for ST >= 1
+  constexpr int nb = 1 << ST;
 #pragma unroll
-  for (int blk = 0; blk < (1 << ST); blk++) {
-    const TwPair t = ld_tw(tw + base + blk);
+  for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
+    TwPair t[2];
+    if constexpr (nb > 1)
+      ld_tw2(tw + base + blk, t[0], t[1]);
+    else
+      t[0] = ld_tw(tw + base);
 #pragma unroll
-    for (int u0 = 0; u0 < h; u0++) {
-      ct_bfly(va[blk * 2 * h + u0], va[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
-      ct_bfly(vb[blk * 2 * h + u0], vb[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
-    }
+    for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
+#pragma unroll
+      for (int u0 = 0; u0 < h; u0++) {
+        const int i0 = (blk + e) * 2 * h + u0;
+        ct_bfly(va[i0], va[i0 + h], t[e].w, t[e].wp, q, two_q);
+        ct_bfly(vb[i0], vb[i0 + h], t[e].w, t[e].wp, q, two_q);
+      }
   }
 }
 
@@ -89,13 +110,23 @@ __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __re
                                            uint32_t logn, uint32_t sig0, uint32_t g,
                                            uint64_t q, uint64_t two_q, uint64_t hq) {
   constexpr int h = 1 << ST;
+  // base is even whenever the stage needs more than one twiddle (ST <= 2):
+  // logn - sig0 - ST - 1 >= 1 there, and g << (3 - ST) is even
   const uint32_t base = (1u << (logn - sig0 - ST - 1)) + (g << (3 - ST));
+  constexpr int nb = 8 >> ST;
 #pragma unroll
-  for (int blk = 0; blk < (8 >> ST); blk++) {
-    const TwPair t = ld_tw(tw + base + blk);
+  for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
+    TwPair t[2];
+    if constexpr (nb > 1)
+      ld_tw2(tw + base + blk, t[0], t[1]);
+    else
+      t[0] = ld_tw(tw + base);
 #pragma unroll
-    for (int u0 = 0; u0 < h; u0++)
-      gs_bfly_mode<HALVE>(v[blk * 2 * h + u0], v[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q, hq);
+    for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
+#pragma unroll
+      for (int u0 = 0; u0 < h; u0++)
+        gs_bfly_mode<HALVE>(v[(blk + e) * 2 * h + u0], v[(blk + e) * 2 * h + u0 + h], t[e].w,
+                            t[e].wp, q, two_q, hq);
   }
 }
 
@@ -119,12 +150,20 @@ __device__ __forceinline__ void ct_col_stage(uint64_t (&x)[R], const TwPair* __r
                                              uint64_t q, uint64_t two_q) {
   if constexpr ((1 << S) < R) {
     constexpr int h = R >> (S + 1);
+    constexpr int nb = 1 << S;
 #pragma unroll
-    for (int blk = 0; blk < (1 << S); blk++) {
-      const TwPair t = ld_tw(tw + (1u << S) + blk);
+    for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
+      TwPair t[2];
+      if constexpr (nb > 1)
+        ld_tw2(tw + nb + blk, t[0], t[1]);  // index nb + blk is even
+      else
+        t[0] = ld_tw(tw + 1);
 #pragma unroll
-      for (int u0 = 0; u0 < h; u0++)
-        ct_bfly(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, q, two_q);
+      for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
+#pragma unroll
+        for (int u0 = 0; u0 < h; u0++)
+          ct_bfly(x[(blk + e) * 2 * h + u0], x[(blk + e) * 2 * h + u0 + h], t[e].w, t[e].wp, q,
+                  two_q);
     }
     ct_col_stage<R, S + 1>(x, tw, q, two_q);
   }
@@ -149,13 +188,20 @@ __device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __r
 #pragma unroll
       for (int u0 = 0; u0 < h; u0++) gs_bfly_last(x[u0], x[u0 + h], K);
     } else {
+      constexpr int nb = R / (2 * h);  // table index nb + blk, even when nb > 1
 #pragma unroll
-      for (int blk = 0; blk < R / (2 * h); blk++) {
-        const TwPair t = ld_tw(tw + (R >> (E + 1)) + blk);
+      for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
+        TwPair t[2];
+        if constexpr (nb > 1)
+          ld_tw2(tw + nb + blk, t[0], t[1]);
+        else
+          t[0] = ld_tw(tw + 1);
 #pragma unroll
-        for (int u0 = 0; u0 < h; u0++)
-          gs_bfly_mode<HALVE>(x[blk * 2 * h + u0], x[blk * 2 * h + u0 + h], t.w, t.wp, K.q,
-                              K.two_q, K.half_q1);
+        for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
+#pragma unroll
+          for (int u0 = 0; u0 < h; u0++)
+            gs_bfly_mode<HALVE>(x[(blk + e) * 2 * h + u0], x[(blk + e) * 2 * h + u0 + h], t[e].w,
+                                t[e].wp, K.q, K.two_q, K.half_q1);
       }
     }
     gs_col_stage<R, E + 1, HALVE>(x, tw, K);
@@ -206,40 +252,57 @@ struct PassGeo {
   uint32_t g;    // block index of the group within the whole transform
 };
 
-// With the padding p(j) = j + (j >> 4), the padded index of word u of a
+// With the padding p(j) = j + 2 floor(j/16), the padded index of word u of a
 // group is pbase + off(u) with a compile-time offset per layout:
-//   layout 0: 272 u;  layout 1: 17 u;  layout 2: u.
+//   layout 0: 288 u;  layout 1: 18 u;  layout 2: u.
 template <int L>
 __device__ __forceinline__ constexpr int lay_off(int u) {
-  return L == 0 ? 272 * u : (L == 1 ? 17 * u : u);
+  return L == 0 ? 288 * u : (L == 1 ? 18 * u : u);
 }
 
 __device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
   PassGeo G;
   G.layout = layout;
   if (layout == 0) {
-    G.pbase = th + (th >> 4);
+    G.pbase = th + 2 * (th >> 4);
     G.g = t;
   } else if (layout == 1) {
-    G.pbase = 272 * (th >> 4) + (th & 15);
+    G.pbase = 288 * (th >> 4) + (th & 15);
     G.g = t * 16 + (th >> 4);
   } else {
-    G.pbase = 17 * th;
+    G.pbase = 18 * th;
     G.g = t * 256 + th;
   }
   return G;
 }
 
+// Layout 2 moves its 16 consecutive words as 8 16-byte pairs.
 template <int L>
 __device__ __forceinline__ void ld16(uint64_t (&v)[16], const uint64_t* s) {
+  if constexpr (L == 2) {
+    const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(s);
 #pragma unroll
-  for (int u = 0; u < 16; u++) v[u] = s[lay_off<L>(u)];
+    for (int k = 0; k < 8; k++) {
+      const ulonglong2 w = s2[k];
+      v[2 * k] = w.x;
+      v[2 * k + 1] = w.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = s[lay_off<L>(u)];
+  }
 }
 
 template <int L>
 __device__ __forceinline__ void st16(uint64_t* s, const uint64_t (&v)[16]) {
+  if constexpr (L == 2) {
+    ulonglong2* s2 = reinterpret_cast<ulonglong2*>(s);
 #pragma unroll
-  for (int u = 0; u < 16; u++) s[lay_off<L>(u)] = v[u];
+    for (int k = 0; k < 8; k++) s2[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 16; u++) s[lay_off<L>(u)] = v[u];
+  }
 }
 
 __device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
@@ -348,7 +411,10 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
                                           uint64_t* sb, const TwPair* __restrict__ twf,
                                           uint32_t logn, uint32_t t, int th, uint64_t q,
                                           uint64_t two_q, bool trunc = false) {
-#pragma unroll 1
+  // unrolled: with the layout of every pass known at compile time the
+  // scheduler interleaves the two operands' loads and butterflies across
+  // the pass (measured faster than the rolled loop here, unlike rows_fwd)
+#pragma unroll
   for (int p = 0; p < 3; p++) {
     const PassGeo G = pass_geo(p, th, t);
     if (p == 0) {
@@ -398,18 +464,56 @@ __device__ __forceinline__ void fused_pair(uint64_t& x0, uint64_t& x1, uint64_t 
 // The fused step on the 8 pairs (u, u+1) of a layout-2 register group (group
 // g = 256 t + th holds bit-reversed positions 16 g + u): pair i = 8 g + u/2,
 // so floor(i/2) = 4 g + u/4 and i is odd when u/2 is.  Result in va.  The
-// step is symmetric in the two operands; vb may be a register array or a
-// pointer to the other operand's words (read once each).
-template <typename VB>
-__device__ __forceinline__ void fused_pairs16(uint64_t (&va)[16], const VB& vb,
+// step is symmetric in the two operands; the other operand comes from
+// registers (vb) or from its layout-2 words in shared memory (sb, 16-byte
+// pairs).
+__device__ __forceinline__ void fused_pairs16(uint64_t (&va)[16], const uint64_t (&vb)[16],
                                               const TwPair* __restrict__ twf, uint32_t logn,
                                               uint32_t g, const LimbConst& K) {
-  const uint32_t base = (1u << (logn - 2)) + 4 * g;
+  const uint32_t base = (1u << (logn - 2)) + 4 * g;  // even
 #pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const TwPair w = ld_tw(twf + base + k);
-    fused_pair<false>(va[4 * k], va[4 * k + 1], vb[4 * k], vb[4 * k + 1], w, K);
-    fused_pair<true>(va[4 * k + 2], va[4 * k + 3], vb[4 * k + 2], vb[4 * k + 3], w, K);
+  for (int k = 0; k < 4; k += 2) {
+    TwPair w[2];
+    ld_tw2(twf + base + k, w[0], w[1]);
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const int u = 4 * (k + e);
+      fused_pair<false>(va[u], va[u + 1], vb[u], vb[u + 1], w[e], K);
+      fused_pair<true>(va[u + 2], va[u + 3], vb[u + 2], vb[u + 3], w[e], K);
+    }
+  }
+}
+
+__device__ __forceinline__ void fused_pairs16_smem(uint64_t (&va)[16], const uint64_t* sb,
+                                                   const TwPair* __restrict__ twf,
+                                                   uint32_t logn, uint32_t g, const LimbConst& K) {
+  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+  const uint32_t base = (1u << (logn - 2)) + 4 * g;  // even
+#pragma unroll
+  for (int k = 0; k < 4; k += 2) {
+    TwPair w[2];
+    ld_tw2(twf + base + k, w[0], w[1]);
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+      const int u = 4 * (k + e);
+      const ulonglong2 y0 = s2[u / 2], y1 = s2[u / 2 + 1];
+      fused_pair<false>(va[u], va[u + 1], y0.x, y0.y, w[e], K);
+      fused_pair<true>(va[u + 2], va[u + 3], y1.x, y1.y, w[e], K);
+    }
+  }
+}
+
+// Algorithm 4 products of a register group with the other operand's
+// layout-2 words in shared memory (16-byte pairs).
+__device__ __forceinline__ void pointwise16(uint64_t (&v)[16], const uint64_t* sb,
+                                            const LimbConst& K) {
+  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const ulonglong2 y = s2[k];
+    v[2 * k] = mul_barrett_alg4(reduce4(y.x, K.q, K.two_q), reduce4(v[2 * k], K.q, K.two_q), K);
+    v[2 * k + 1] =
+        mul_barrett_alg4(reduce4(y.y, K.q, K.two_q), reduce4(v[2 * k + 1], K.q, K.two_q), K);
   }
 }
 
@@ -469,13 +573,10 @@ __device__ __forceinline__ void row_task_polymul(const uint64_t* ga, const uint6
   // product step in bit-reversed order (Algorithm 4 products, or Algorithm
   // 8's pair step); each thread re-reads only the words it stored itself
   const uint64_t* a2 = sa + G2.pbase;
-  if (fused) {
-    fused_pairs16(v, a2, twf, logn, G2.g, K);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 16; u++)
-      v[u] = mul_barrett_alg4(reduce4(a2[u], K.q, K.two_q), reduce4(v[u], K.q, K.two_q), K);
-  }
+  if (fused)
+    fused_pairs16_smem(v, a2, twf, logn, G2.g, K);
+  else
+    pointwise16(v, a2, K);
   rows_inv<HALVE>(v, gc, single, sa, twi, logn, t, th, K, fused);
 }
 

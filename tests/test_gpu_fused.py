@@ -12,16 +12,18 @@ pytestmark = pytest.mark.gpu
 FUSED_LOG2N = list(range(2, 18))
 
 
-def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None, row_ops=1):
+def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None):
+    """variant: None (the plan's default launch) or (variant, row_ops)."""
     from paper_2209_01290_gb300 import Plan, capi
     qs, psis = capi.pm_find_params(log2n, nlimbs, qbits)
     plan = Plan(1 << log2n, qs, psis, halving=halving, fused=True)
-    if variant is not None or row_ops != 1:
-        capi.pm_plan_tune(plan.handle, variant or 0, row_ops=row_ops)
+    if variant is not None:
+        capi.pm_plan_tune(plan.handle, variant[0], row_ops=variant[1])
     return plan, qs, psis
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["split", "persistent"])
+@pytest.mark.parametrize("variant", [(0, 1), (0, 2), (1, 1)],
+                         ids=["split-rows1", "split-rows2", "persistent"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold2N", "halving"])
 @pytest.mark.parametrize("log2n", FUSED_LOG2N)
 def test_fused_all_sizes(oracle, log2n, halving, variant):
@@ -48,10 +50,11 @@ def test_fused_matches_alg8_oracle(oracle, log2n):
 
 @pytest.mark.parametrize("halving", [False, True], ids=["fold2N", "halving"])
 @pytest.mark.parametrize("log2n", [12, 14, 16, 17])
-def test_fused_rows_together(oracle, log2n, halving):
-    """Row kernel with both operands in registers (row_ops = 2)."""
+def test_fused_rows_one_after_other(oracle, log2n, halving):
+    """Row kernel with the operands transformed one after the other
+    (row_ops = 1), one limb pair per product."""
     n = 1 << log2n
-    plan, qs, psis = _plan(log2n, 2, halving=halving, row_ops=2)
+    plan, qs, psis = _plan(log2n, 2, halving=halving, variant=(0, 1))
     a, b = operands(43000 + log2n, qs, 1, n)
     got = to_host(plan.polymul(to_dev(a), to_dev(b)))
     assert np.array_equal(got, oracle_polymul_batch(oracle, a, b, qs, psis))

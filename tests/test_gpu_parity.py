@@ -21,22 +21,28 @@ def torch_cuda():
 
 
 def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None):
+    """variant: None (the plan's default launch) or (variant, row_ops)."""
     from paper_2209_01290_gb300 import Plan, capi
     qs, psis = capi.pm_find_params(log2n, nlimbs, qbits)
     plan = Plan(1 << log2n, qs, psis, halving=halving)
     if variant is not None:
-        capi.pm_plan_tune(plan.handle, variant)
+        capi.pm_plan_tune(plan.handle, variant[0], row_ops=variant[1])
     return plan, qs, psis
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["split", "persistent"])
+VARIANTS = [(0, 1), (0, 2), (1, 1)]
+VARIANT_IDS = ["split-rows1", "split-rows2", "persistent"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
 @pytest.mark.parametrize("halving", [False, True], ids=["fold1N", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
 def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving, variant):
     """Every code path: radix-2 smem kernel (N <= 2^11), single-row kernel
     (2^12), one-CTA 2^13 kernel, column split (2^14..2^17) as three launches
-    or as one persistent work-queue launch (2^13..2^17); 2 polys x 3 limbs;
-    1/N folded into the last stage or applied as per-stage halving."""
+    (row kernel with the operands one after the other or together) or as one
+    persistent work-queue launch (2^13..2^17); 2 polys x 3 limbs; 1/N folded
+    into the last stage or applied as per-stage halving."""
     n = 1 << log2n
     L, P = (3, 2) if log2n <= 15 else (2, 1)
     plan, qs, psis = _plan(log2n, L, halving=halving, variant=variant)
