@@ -287,7 +287,10 @@ def run_gpu(args):
         dom_idx, dom_name = 0, "k_persist (whole polymul, one persistent launch)"
         dom_mulmods = mulmods_per_polymul(log2n) * units
     elif log2n >= 14:
-        dom_idx, dom_name = 1, "k_rows<POLYMUL> (in-row stages + Barrett pointwise)"
+        dom_idx = 1
+        dom_name = ("k_rows2<POLYMUL> (in-row stages of a and b together, Barrett pointwise, "
+                    "inverse in-row stages)" if tuning.row_ops == 2 else
+                    "k_rows<POLYMUL> (in-row stages + Barrett pointwise)")
         dom_mulmods = rows_kernel_mulmods(log2n) * units
     else:
         dom_idx, dom_name = 0, "fused single-kernel polymul"
@@ -315,7 +318,9 @@ def run_gpu(args):
         if nphase == 4 else {"single_launch": avg_phase[0]},
         "roofline": {"bound": "alu", "kernel": dom_name, "achieved": achieved / 1e12,
                      "peak": peak_mulmod / 1e12, "unit": "Tmulmod/s",
-                     "frac": achieved / peak_mulmod, "traffic": None,
+                     "frac": achieved / peak_mulmod,
+                     "traffic": kernel_traffic(dom_name.split(" ")[0], log2n, units,
+                                               args.fused, persistent),
                      "peak_source": "measured register-resident 60-bit Shoup mulmod rate "
                                     "(pm_measure_peaks, same process)",
                      "imad_peak_tops": peak_imad / 1e12,
@@ -333,6 +338,35 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def kernel_sources_sha1() -> str:
+    """Hash of the CUDA sources the kernels are built from."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2209_01290_gb300",
+                        "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(kernel: str, log2n: int, units: int, fused: bool, persistent: bool):
+    """DRAM bytes (read + write) per launch of the dominant kernel, from the
+    committed ncu figure in profiles/traffic.json scaled by the units this
+    launch processes; None when there is no figure for this kernel and N or
+    the kernel sources changed since it was captured."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+    if persistent or fused or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        table = json.load(fh)
+    ent = table.get(f"{kernel} N=2^{log2n}")
+    if not ent or ent.get("source_sha1") != kernel_sources_sha1():
+        return None
+    return ent["dram_bytes_per_unit"] * units
 
 
 # ------------------------------------------------------------------ workloads
