@@ -577,6 +577,33 @@ def run_workload(args):
                 res[k + "_polymuls_per_s"] = P / (ms * 1e-3)
             res["alg8_speedup"] = res["eq2_ms"] / res["alg8_ms"]
             lines.append(res)
+    elif args.workload == "word32":
+        # 30-bit primes: 32-bit words (PM_PLAN_WORD32) vs the same primes in
+        # 64-bit words; batched products (~1 GiB of 64-bit operands per step)
+        for log2n in range(12, 18):
+            n = 1 << log2n
+            qs, psis = capi.pm_find_params(log2n, 1, 30)
+            P = max(1, (1 << 26) // n)
+            A = inputs.uniform_limbs_torch(log2n, qs, P, n, device=dev)
+            B = inputs.uniform_limbs_torch(log2n + 100, qs, P, n, device=dev)
+            A32, B32 = A.to(torch.int32), B.to(torch.int32)
+            C, C32 = torch.empty_like(A), torch.empty_like(A32)
+            p64, p32 = Plan(n, qs, psis), Plan(n, qs, psis, word32=True)
+            res = {"workload": f"30-bit primes, N=2^{log2n}, {P} products per step", "N": n,
+                   "products": P, "q": qs[0]}
+            for name, plan, x, y, z in [("w64", p64, A, B, C), ("w32", p32, A32, B32, C32)]:
+                plan.reserve(P, stream=st)
+                for _ in range(args.warmup):
+                    plan.polymul(x, y, out=z, stream=st)
+                t = _time_each(lambda: plan.polymul(x, y, out=z, stream=st), 10, st)
+                ms = float(np.median(t))
+                res[name + "_ms"] = ms
+                res[name + "_polymuls_per_s"] = P / (ms * 1e-3)
+                tf = _time_each(lambda: plan.ntt_fwd_(z, stream=st), 10, st)
+                res[name + "_ntt_fwd_us_per_ntt"] = float(np.median(tf)) * 1e3 / P
+            res["same_products"] = bool(torch.equal(C32.to(torch.int64) & 0xFFFFFFFF, C))
+            res["w32_speedup"] = res["w64_ms"] / res["w32_ms"]
+            lines.append(res)
     for line in lines:
         print(json.dumps(line), flush=True)
     return 0
@@ -667,7 +694,7 @@ def main():
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom",
-                             "fused"])
+                             "fused", "word32"])
     ap.add_argument("--fused", action="store_true",
                     help="headline products by Algorithm 8 (PM_PLAN_FUSED)")
     ap.add_argument("--tom-count", type=int, default=1 << 15)

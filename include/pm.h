@@ -112,7 +112,17 @@ enum {
      * the calls built on it (graphs, uneven batches, serving, host pipeline)
      * change; pm_ntt_fwd / pm_ntt_inv / pm_pointwise stay full transforms.
      * Needs N >= 4 (log2n >= 2): pm_plan_create_ex gives PM_ERR_N for N = 2. */
-    PM_PLAN_FUSED = 2
+    PM_PLAN_FUSED = 2,
+    /* 32-bit words: every q must be below 2^30 (Algorithm 4 with a 32-bit
+     * word, m <= beta - 2), coefficients are uint32_t and the twiddle tables
+     * hold 32-bit words with 32-bit Shoup companions (Table 4's 30-bit
+     * setting).  Such a plan takes the *32 calls below (pm_ntt_fwd32,
+     * pm_ntt_inv32, pm_pointwise32, pm_polymul32, pm_check_reduced32) and is
+     * refused (PM_ERR_ARG) by the uint64_t calls, the persistent variant,
+     * graphs, uneven batches, the server and the host pipeline; the
+     * uint64_t calls refuse it the other way round.  Combines with
+     * PM_PLAN_HALVING and PM_PLAN_FUSED. */
+    PM_PLAN_WORD32 = 4
 };
 
 /* pm_plan_create with options: `flags` is a combination of PM_PLAN_*;
@@ -158,6 +168,20 @@ pm_status pm_pointwise(const pm_plan *plan, const uint64_t *d_a, const uint64_t 
  * (each unit reads all of its inputs before it writes any output). */
 pm_status pm_polymul(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
                      uint64_t *d_c, uint32_t npoly, void *stream);
+
+/* ---- 32-bit words (plans created with PM_PLAN_WORD32, q < 2^30).
+ * The same operations as pm_ntt_fwd, pm_ntt_inv, pm_pointwise, pm_polymul
+ * and pm_check_reduced (same layout [npoly][nlimbs][N], same ownership,
+ * aliasing and error rules) on uint32_t arrays; 16-byte aligned device
+ * pointers.  A 64-bit plan gives PM_ERR_ARG. */
+pm_status pm_ntt_fwd32(const pm_plan *plan, uint32_t *d_x, uint32_t npoly, void *stream);
+pm_status pm_ntt_inv32(const pm_plan *plan, uint32_t *d_x, uint32_t npoly, void *stream);
+pm_status pm_pointwise32(const pm_plan *plan, const uint32_t *d_a, const uint32_t *d_b,
+                         uint32_t *d_c, uint32_t npoly, void *stream);
+pm_status pm_polymul32(const pm_plan *plan, const uint32_t *d_a, const uint32_t *d_b,
+                       uint32_t *d_c, uint32_t npoly, void *stream);
+pm_status pm_check_reduced32(const pm_plan *plan, const uint32_t *d_x, uint32_t npoly,
+                             void *stream);
 
 /* Same product as pm_polymul, for callers that must not allocate device
  * memory: code running while another memory manager owns the device pool,

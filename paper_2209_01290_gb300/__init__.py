@@ -43,14 +43,18 @@ class Plan:
     """A device-resident plan for one (N, {q_l}, {psi_l})."""
 
     def __init__(self, n: int, qs, psis=None, device: int = 0, halving: bool = False,
-                 fused: bool = False):
+                 fused: bool = False, word32: bool = False):
         """halving=True scales by 1/2 at every inverse butterfly (the paper's
         Eq. 2 form); the default folds 1/N into the last inverse stage.
-        fused=True computes products by Algorithm 8 (N >= 4)."""
+        fused=True computes products by Algorithm 8 (N >= 4).
+        word32=True: 32-bit words (every q < 2^30); the tensors are int32
+        (bit patterns of uint32) instead of int64."""
         self.n = n
         self.log2n = _log2(n)
         self.device = device
-        flags = (capi.PM_PLAN_HALVING if halving else 0) | (capi.PM_PLAN_FUSED if fused else 0)
+        self.word32 = word32
+        flags = ((capi.PM_PLAN_HALVING if halving else 0) | (capi.PM_PLAN_FUSED if fused else 0)
+                 | (capi.PM_PLAN_WORD32 if word32 else 0))
         self._h = capi.pm_plan_create_ex(self.log2n, list(qs), psis, device, flags)
         _, self.nlimbs, self.qs, self.psis = capi.pm_plan_info(self._h)
 
@@ -83,8 +87,9 @@ class Plan:
         import torch
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError("expected a CUDA tensor")
-        if t.dtype not in (torch.int64, torch.uint64):
-            raise TypeError(f"expected int64/uint64, got {t.dtype}")
+        want = (torch.int32,) if self.word32 else (torch.int64, torch.uint64)
+        if t.dtype not in want:
+            raise TypeError(f"expected {'int32' if self.word32 else 'int64/uint64'}, got {t.dtype}")
         if not t.is_contiguous():
             raise ValueError("tensor must be contiguous")
         if t.device.index != self.device:
@@ -97,12 +102,14 @@ class Plan:
     # -- hot path
     def ntt_fwd_(self, x, stream=None):
         npoly = self._npoly(x)
-        capi.pm_ntt_fwd(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+        fn = capi.pm_ntt_fwd32 if self.word32 else capi.pm_ntt_fwd
+        fn(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
         return x
 
     def ntt_inv_(self, x, stream=None):
         npoly = self._npoly(x)
-        capi.pm_ntt_inv(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+        fn = capi.pm_ntt_inv32 if self.word32 else capi.pm_ntt_inv
+        fn(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
         return x
 
     def pointwise(self, a, b, out=None, stream=None):
@@ -113,8 +120,8 @@ class Plan:
         out = torch.empty_like(a) if out is None else out
         if self._npoly(out) != npoly:
             raise ValueError("out has the wrong size")
-        capi.pm_pointwise(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly,
-                          _stream_handle(stream))
+        fn = capi.pm_pointwise32 if self.word32 else capi.pm_pointwise
+        fn(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly, _stream_handle(stream))
         return out
 
     def polymul(self, a, b, out=None, stream=None):
@@ -125,8 +132,8 @@ class Plan:
         out = torch.empty_like(a) if out is None else out
         if self._npoly(out) != npoly:
             raise ValueError("out has the wrong size")
-        capi.pm_polymul(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly,
-                        _stream_handle(stream))
+        fn = capi.pm_polymul32 if self.word32 else capi.pm_polymul
+        fn(self.handle, a.data_ptr(), b.data_ptr(), out.data_ptr(), npoly, _stream_handle(stream))
         return out
 
     def polymul_host(self, h_a, h_b, h_c, d_a, d_b, d_c, stream=None):
@@ -153,7 +160,8 @@ class Plan:
 
     def check_reduced(self, x, stream=None) -> bool:
         npoly = self._npoly(x)
-        return capi.pm_check_reduced(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
+        fn = capi.pm_check_reduced32 if self.word32 else capi.pm_check_reduced
+        return fn(self.handle, x.data_ptr(), npoly, _stream_handle(stream))
 
     def sync(self, stream=None) -> None:
         capi.pm_plan_sync(self.handle, _stream_handle(stream))

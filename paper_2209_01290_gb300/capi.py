@@ -39,6 +39,11 @@ SIGNATURES = {
     "pm_polymul_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_polymul_noalloc": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
     "pm_check_reduced": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_ntt_fwd32": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_ntt_inv32": (_i32, [_vp, _vp, _u32, _vp]),
+    "pm_pointwise32": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_polymul32": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp]),
+    "pm_check_reduced32": (_i32, [_vp, _vp, _u32, _vp]),
     "pm_plan_sync": (_i32, [_vp, _vp]),
     "pm_plan_tune": (_i32, [_vp, ctypes.c_void_p]),
     "pm_plan_inject_fault": (_i32, [_vp, _i32]),
@@ -123,6 +128,7 @@ def pm_find_params(log2n: int, nlimbs: int, qbits: int = 60):
 
 PM_PLAN_HALVING = 1
 PM_PLAN_FUSED = 2
+PM_PLAN_WORD32 = 4
 
 
 def pm_plan_create(log2n: int, qs, psis=None, device: int = 0) -> int:
@@ -194,6 +200,31 @@ def pm_check_reduced(plan: int, d_x: int, npoly: int, stream: int = 0) -> bool:
     if st == -10:
         return False
     check(st, "pm_check_reduced")
+    return True
+
+
+# 32-bit words (plans with PM_PLAN_WORD32): the same calls on uint32 arrays.
+def pm_ntt_fwd32(plan: int, d_x: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_ntt_fwd32", plan, d_x, npoly, stream)
+
+
+def pm_ntt_inv32(plan: int, d_x: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_ntt_inv32", plan, d_x, npoly, stream)
+
+
+def pm_pointwise32(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_pointwise32", plan, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_polymul32(plan: int, d_a: int, d_b: int, d_c: int, npoly: int, stream: int = 0) -> None:
+    _call("pm_polymul32", plan, d_a, d_b, d_c, npoly, stream)
+
+
+def pm_check_reduced32(plan: int, d_x: int, npoly: int, stream: int = 0) -> bool:
+    st = load().pm_check_reduced32(plan, d_x, npoly, stream)
+    if st == -10:
+        return False
+    check(st, "pm_check_reduced32")
     return True
 
 

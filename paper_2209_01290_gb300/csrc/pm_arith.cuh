@@ -1,11 +1,16 @@
-// pm_arith.cuh -- device modular arithmetic for 64-bit words and moduli
-// q < 2^62 (arxiv 2209.01290, Sec. II).
+// pm_arith.cuh -- device modular arithmetic (arxiv 2209.01290, Sec. II) for
+// two word sizes:
+//   64-bit words, moduli q < 2^62 (Algorithm 4 with beta = 64);
+//   32-bit words, moduli q < 2^30 (Algorithm 4 with beta = 32).
 //
 // Value ranges ("lazy" representatives, Harvey-style) used by the butterflies:
 //   forward CT butterfly : inputs and outputs in [0, 4q)
 //   inverse GS butterfly : inputs and outputs in [0, 2q)
-// q < 2^62 keeps 4q < 2^64, so no word ever overflows.  Results that leave
-// the library are reduced to the canonical range [0, q).
+// q < 2^(beta-2) keeps 4q < 2^beta, so no word ever overflows.  Results that
+// leave the library are reduced to the canonical range [0, q).
+//
+// The functions are templates over the word type W (uint64_t or uint32_t);
+// WordT<W> names the matching twiddle-pair and limb-constant types.
 #pragma once
 #include <cstdint>
 
@@ -13,91 +18,123 @@
 
 namespace pm {
 
+template <typename W>
+struct WordT;
+template <>
+struct WordT<uint64_t> {
+  using Tw = TwPair;
+  using LC = LimbConst;
+  using SW = int64_t;
+};
+template <>
+struct WordT<uint32_t> {
+  using Tw = TwPair32;
+  using LC = LimbConst32;
+  using SW = int32_t;
+};
+
 __device__ __forceinline__ TwPair ld_tw(const TwPair* __restrict__ p) {
   ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(p));
   return TwPair{v.x, v.y};
 }
 
-// Two consecutive twiddle pairs p[0], p[1] in one 256-bit read-only load.
-// p must be 32-byte aligned: every caller passes an even index into a table
-// whose base is 32-byte aligned (cudaMalloc'ed, per-limb offsets N * 16 B).
+__device__ __forceinline__ TwPair32 ld_tw(const TwPair32* __restrict__ p) {
+  uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+  return TwPair32{v.x, v.y};
+}
+
+// Two consecutive twiddle pairs p[0], p[1] in one read-only load (256 bits
+// for 64-bit words, 128 bits for 32-bit words).  p must be aligned to twice
+// the pair size: every caller passes an even index into a table whose base
+// is so aligned (cudaMalloc'ed, per-limb offsets N pairs).
 __device__ __forceinline__ void ld_tw2(const TwPair* __restrict__ p, TwPair& t0, TwPair& t1) {
   asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
       : "=l"(t0.w), "=l"(t0.wp), "=l"(t1.w), "=l"(t1.wp)
       : "l"(p));
 }
 
-// w * y mod q up to one multiple of q (Shoup): for w < q and any 64-bit y,
-// the result is congruent to w*y and lies in [0, 2q).  Written as
-// w*y + qh*(2^64 - q) mod 2^64 so that the subtraction folds into the
-// multiply-add chain of the low-word products.
-__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint64_t wp,
-                                                   uint64_t q) {
-  const uint64_t qh = __umul64hi(wp, y);
-  return w * y + qh * (0 - q);
+__device__ __forceinline__ void ld_tw2(const TwPair32* __restrict__ p, TwPair32& t0,
+                                       TwPair32& t1) {
+  const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+  t0 = TwPair32{v.x, v.y};
+  t1 = TwPair32{v.z, v.w};
 }
 
-// x - m if x >= m else x, for x < 2^63 + m and m <= 2^63 (all lazy values here
-// are < 2^62): the sign of x - m decides, one compare on the high word.
-__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) {
-  const uint64_t t = x - m;
-  return (int64_t)t < 0 ? x : t;
+__device__ __forceinline__ uint64_t mulhi(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+__device__ __forceinline__ uint32_t mulhi(uint32_t a, uint32_t b) { return __umulhi(a, b); }
+
+// w * y mod q up to one multiple of q (Shoup): for w < q and any word y, the
+// result is congruent to w*y and lies in [0, 2q).  Written as
+// w*y + qh*(2^beta - q) mod 2^beta so that the subtraction folds into the
+// multiply-add chain of the low-word products.
+template <typename W>
+__device__ __forceinline__ W mul_shoup_lazy(W y, W w, W wp, W q) {
+  const W qh = mulhi(wp, y);
+  return w * y + qh * (W(0) - q);
+}
+
+// x - m if x >= m else x, for x < 2^(beta-1) + m and m <= 2^(beta-1) (all
+// lazy values here are < 2^(beta-2)): the sign of x - m decides.
+template <typename W>
+__device__ __forceinline__ W csub(W x, W m) {
+  const W t = x - m;
+  return (typename WordT<W>::SW)t < 0 ? x : t;
 }
 
 // Merged-CT butterfly (Algorithm 6 body):
 //   (x, y) <- (x + w y, x - w y) mod q
 // on lazy representatives in [0, 4q).
-__device__ __forceinline__ void ct_bfly(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
-                                        uint64_t q, uint64_t two_q) {
-  const uint64_t a = csub(x, two_q);               // [0, 2q)
-  const uint64_t t = mul_shoup_lazy(y, w, wp, q);  // [0, 2q)
-  x = a + t;                                       // [0, 4q)
-  y = a - t + two_q;                               // (0, 4q)
+template <typename W>
+__device__ __forceinline__ void ct_bfly(W& x, W& y, W w, W wp, W q, W two_q) {
+  const W a = csub(x, two_q);               // [0, 2q)
+  const W t = mul_shoup_lazy(y, w, wp, q);  // [0, 2q)
+  x = a + t;                                // [0, 4q)
+  y = a - t + two_q;                        // (0, 4q)
 }
 
 // x/2 mod q for x in [0, 2q): x >> 1 plus (q+1)/2 when x is odd (Sec. III-A).
 // Result in [0, 2q).
-__device__ __forceinline__ uint64_t half_lazy(uint64_t x, uint64_t half_q1) {
-  return (x >> 1) + ((x & 1) ? half_q1 : 0);
+template <typename W>
+__device__ __forceinline__ W half_lazy(W x, W half_q1) {
+  return (x >> 1) + ((x & 1) ? half_q1 : W(0));
 }
 
 // Merged-GS butterfly (Algorithm 7 body) with the 1/2 scaling of Eq. 2:
 //   (x, y) <- ((x + y)/2, w (x - y)/2) mod q
 // w2 = w * 2^-1 mod q is the table entry, so the second output needs no
 // separate halving.  Lazy representatives in [0, 2q).
-__device__ __forceinline__ void gs_bfly_half(uint64_t& x, uint64_t& y, uint64_t w2,
-                                             uint64_t w2p, uint64_t q, uint64_t two_q,
-                                             uint64_t half_q1) {
-  const uint64_t s = csub(x + y, two_q);           // [0, 2q)
-  const uint64_t d = x - y + two_q;                // (0, 4q)
-  x = half_lazy(s, half_q1);                       // [0, 2q)
-  y = mul_shoup_lazy(d, w2, w2p, q);               // [0, 2q)
+template <typename W>
+__device__ __forceinline__ void gs_bfly_half(W& x, W& y, W w2, W w2p, W q, W two_q, W half_q1) {
+  const W s = csub(x + y, two_q);           // [0, 2q)
+  const W d = x - y + two_q;                // (0, 4q)
+  x = half_lazy(s, half_q1);                // [0, 2q)
+  y = mul_shoup_lazy(d, w2, w2p, q);        // [0, 2q)
 }
 
 // Merged-GS butterfly (Algorithm 7 body) without scaling:
 //   (x, y) <- (x + y, w (x - y)) mod q
 // on lazy representatives in [0, 2q); 1/N is applied by gs_bfly_last.
-__device__ __forceinline__ void gs_bfly(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
-                                        uint64_t q, uint64_t two_q) {
-  const uint64_t s = csub(x + y, two_q);           // [0, 2q)
-  const uint64_t d = x - y + two_q;                // (0, 4q)
+template <typename W>
+__device__ __forceinline__ void gs_bfly(W& x, W& y, W w, W wp, W q, W two_q) {
+  const W s = csub(x + y, two_q);           // [0, 2q)
+  const W d = x - y + two_q;                // (0, 4q)
   x = s;
-  y = mul_shoup_lazy(d, w, wp, q);                 // [0, 2q)
+  y = mul_shoup_lazy(d, w, wp, q);          // [0, 2q)
 }
 
 // The last GS stage (k = N/2, twiddle Psi^-1_br[1]) with 1/N folded in:
 //   (x, y) <- ((x + y) / N, w (x - y) / N) mod q, results in [0, 2q).
-__device__ __forceinline__ void gs_bfly_last(uint64_t& x, uint64_t& y, const LimbConst& k) {
-  const uint64_t s = x + y;                        // [0, 4q)
-  const uint64_t d = x - y + k.two_q;              // (0, 4q)
+template <typename W, typename LC>
+__device__ __forceinline__ void gs_bfly_last(W& x, W& y, const LC& k) {
+  const W s = x + y;                        // [0, 4q)
+  const W d = x - y + k.two_q;              // (0, 4q)
   x = mul_shoup_lazy(s, k.ninv, k.ninv_p, k.q);
   y = mul_shoup_lazy(d, k.w1ninv, k.w1ninv_p, k.q);
 }
 
 // One GS butterfly in the plan's scaling mode.
-template <bool HALVE>
-__device__ __forceinline__ void gs_bfly_mode(uint64_t& x, uint64_t& y, uint64_t w, uint64_t wp,
-                                             uint64_t q, uint64_t two_q, uint64_t hq) {
+template <bool HALVE, typename W>
+__device__ __forceinline__ void gs_bfly_mode(W& x, W& y, W w, W wp, W q, W two_q, W hq) {
   if constexpr (HALVE)
     gs_bfly_half(x, y, w, wp, q, two_q, hq);
   else
@@ -105,14 +142,15 @@ __device__ __forceinline__ void gs_bfly_mode(uint64_t& x, uint64_t& y, uint64_t 
 }
 
 // [0, 4q) -> [0, q)
-__device__ __forceinline__ uint64_t reduce4(uint64_t x, uint64_t q, uint64_t two_q) {
+template <typename W>
+__device__ __forceinline__ W reduce4(W x, W q, W two_q) {
   return csub(csub(x, two_q), q);
 }
 
-// Algorithm 4 (the paper's Barrett variant): x = a*b < 2^(2m) for a, b < q,
-//   c = x >> (m-2); quot = (c * mu) >> (m+3); rem = x - quot*q; one correction.
-// The 128-bit quantities are kept as (hi, lo) pairs; only the low word of
-// quot*q is needed because rem < 2q < 2^64.
+// Algorithm 4 (the paper's Barrett variant), beta = 64: x = a*b < 2^(2m) for
+// a, b < q, c = x >> (m-2); quot = (c * mu) >> (m+3); rem = x - quot*q; one
+// correction.  The 128-bit quantities are kept as (hi, lo) pairs; only the
+// low word of quot*q is needed because rem < 2q < 2^64.
 __device__ __forceinline__ uint64_t mul_barrett_alg4(uint64_t a, uint64_t b,
                                                      const LimbConst& k) {
   const uint64_t lo = a * b;
@@ -129,6 +167,18 @@ __device__ __forceinline__ uint64_t mul_barrett_alg4(uint64_t a, uint64_t b,
     quot = (plo >> k.sh2) | (phi << (64 - k.sh2));
   }
   const uint64_t rem = lo - quot * k.q;
+  return csub(rem, k.q);
+}
+
+// Algorithm 4 with beta = 32 (m <= 30): x = a*b < 2^(2m) fits one 64-bit
+// word, c = x >> (m-2) < 2^(m+2) and c*mu < 2^(2m+4) <= 2^64, so every step
+// is a single 64-bit operation; rem < 2q < 2^31 needs only the low words.
+__device__ __forceinline__ uint32_t mul_barrett_alg4(uint32_t a, uint32_t b,
+                                                     const LimbConst32& k) {
+  const uint64_t x = (uint64_t)a * b;
+  const uint64_t c = x >> k.sh1;
+  const uint64_t quot = (c * k.mu) >> k.sh2;
+  const uint32_t rem = (uint32_t)x - (uint32_t)quot * k.q;
   return csub(rem, k.q);
 }
 

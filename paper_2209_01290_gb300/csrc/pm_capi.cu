@@ -119,6 +119,21 @@ pm_status check_plan(const pm_plan* p) {
   return PM_OK;
 }
 
+bool is_word32(const pm_plan* p) { return (p->flags & PM_PLAN_WORD32) != 0; }
+
+// The calls on 64-bit words and their *32 counterparts each take plans of
+// their own word size only.
+pm_status check_word(const pm_plan* p, bool word32, const char* fn) {
+  if (is_word32(p) != word32)
+    return fail(PM_ERR_ARG, "%s: the plan uses %d-bit words", fn, is_word32(p) ? 32 : 64);
+  return PM_OK;
+}
+
+pm_status check_plan_word(const pm_plan* p, bool word32, const char* fn) {
+  pm_status s = check_plan(p);
+  return s != PM_OK ? s : check_word(p, word32, fn);
+}
+
 pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   pm::KParams P{};
   P.twf = p->d_twf;
@@ -130,6 +145,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
   P.row_ops = p->tune.row_ops == 2 ? 2 : 1;
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
+  P.word32 = is_word32(p) ? 1 : 0;
   return P;
 }
 
@@ -215,7 +231,7 @@ void destroy_plan(pm_plan* p) {
 }
 
 bool use_persistent(const pm_plan* p) {
-  return p->tune.variant == PM_VARIANT_PERSISTENT && p->logn >= 13;
+  return p->tune.variant == PM_VARIANT_PERSISTENT && p->logn >= 13 && !is_word32(p);
 }
 
 pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
@@ -293,8 +309,9 @@ pm_status pm_plan_create(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const u
 pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, const uint64_t* q,
                             const uint64_t* psi, int device, uint32_t flags) {
   if (!out) return fail(PM_ERR_ARG, "out is NULL");
-  if (flags & ~(uint32_t)(PM_PLAN_HALVING | PM_PLAN_FUSED))
+  if (flags & ~(uint32_t)(PM_PLAN_HALVING | PM_PLAN_FUSED | PM_PLAN_WORD32))
     return fail(PM_ERR_ARG, "unknown plan flags 0x%x", flags);
+  const bool word32 = (flags & PM_PLAN_WORD32) != 0;
   *out = nullptr;
   if (log2n < 1 || log2n > kMaxLog2N) return fail(PM_ERR_N, "log2n=%u outside [1,17]", log2n);
   if ((flags & PM_PLAN_FUSED) && log2n < 2)
@@ -307,6 +324,9 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
     const uint64_t ql = q[l];
     if (ql <= 3 || ql >= ((uint64_t)1 << 62))
       return fail(PM_ERR_Q, "limb %u: q=%llu outside (3, 2^62)", l, (unsigned long long)ql);
+    if (word32 && ql >= ((uint64_t)1 << 30))
+      return fail(PM_ERR_Q, "limb %u: q=%llu is not below 2^30 (PM_PLAN_WORD32)", l,
+                  (unsigned long long)ql);
     if ((ql - 1) % (2 * n))
       return fail(PM_ERR_Q, "limb %u: q=%llu is not 1 mod 2N (N=%llu)", l, (unsigned long long)ql,
                   (unsigned long long)n);
@@ -354,26 +374,59 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
     return cuda_fail(e, "kernel attributes");
   }
   // limb constants: [0, L) plain; for PM_PLAN_FUSED, [L, 2L) the constants
-  // of Algorithm 8's truncated inverse (2/N in place of 1/N)
+  // of Algorithm 8's truncated inverse (2/N in place of 1/N).  With
+  // PM_PLAN_WORD32 the tables hold the 32-bit types (the device pointers are
+  // reinterpreted by the kernels).
   const uint32_t nlc = (flags & PM_PLAN_FUSED) ? 2 * nlimbs : nlimbs;
-  std::vector<pm::LimbConst> lc(nlc);
-  std::vector<pm::TwPair> twf((size_t)nlimbs * n), twi((size_t)nlimbs * n);
-  for (uint32_t l = 0; l < nlimbs; ++l)
-    pm::host::build_limb(log2n, q[l], psis[l], (flags & PM_PLAN_HALVING) != 0, &lc[l],
-                         &twf[(size_t)l * n], &twi[(size_t)l * n]);
-  for (uint32_t l = nlimbs; l < nlc; ++l) pm::host::fused_limb(lc[l - nlimbs], &lc[l]);
-  const size_t tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair);
-  if ((e = cudaMalloc(&p->d_lc, nlc * sizeof(pm::LimbConst))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_twf, tw_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_twi, tw_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_flag, sizeof(int))) != cudaSuccess) {
+  const bool halving = (flags & PM_PLAN_HALVING) != 0;
+  std::vector<pm::LimbConst> lc;
+  std::vector<pm::TwPair> twf, twi;
+  std::vector<pm::LimbConst32> lc32;
+  std::vector<pm::TwPair32> twf32, twi32;
+  const void *h_lc, *h_twf, *h_twi;
+  size_t lc_bytes, tw_bytes;
+  if (word32) {
+    lc32.resize(nlc);
+    twf32.resize((size_t)nlimbs * n);
+    twi32.resize((size_t)nlimbs * n);
+    for (uint32_t l = 0; l < nlimbs; ++l)
+      pm::host::build_limb32(log2n, q[l], psis[l], halving, &lc32[l], &twf32[(size_t)l * n],
+                             &twi32[(size_t)l * n]);
+    for (uint32_t l = nlimbs; l < nlc; ++l) pm::host::fused_limb32(lc32[l - nlimbs], &lc32[l]);
+    h_lc = lc32.data();
+    h_twf = twf32.data();
+    h_twi = twi32.data();
+    lc_bytes = nlc * sizeof(pm::LimbConst32);
+    tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair32);
+  } else {
+    lc.resize(nlc);
+    twf.resize((size_t)nlimbs * n);
+    twi.resize((size_t)nlimbs * n);
+    for (uint32_t l = 0; l < nlimbs; ++l)
+      pm::host::build_limb(log2n, q[l], psis[l], halving, &lc[l], &twf[(size_t)l * n],
+                           &twi[(size_t)l * n]);
+    for (uint32_t l = nlimbs; l < nlc; ++l) pm::host::fused_limb(lc[l - nlimbs], &lc[l]);
+    h_lc = lc.data();
+    h_twf = twf.data();
+    h_twi = twi.data();
+    lc_bytes = nlc * sizeof(pm::LimbConst);
+    tw_bytes = (size_t)nlimbs * n * sizeof(pm::TwPair);
+  }
+  void *d_lc = nullptr, *d_twf = nullptr, *d_twi = nullptr;
+  e = cudaMalloc(&d_lc, lc_bytes);
+  p->d_lc = (pm::LimbConst*)d_lc;
+  if (e == cudaSuccess) e = cudaMalloc(&d_twf, tw_bytes);
+  p->d_twf = (pm::TwPair*)d_twf;
+  if (e == cudaSuccess) e = cudaMalloc(&d_twi, tw_bytes);
+  p->d_twi = (pm::TwPair*)d_twi;
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_flag, sizeof(int));
+  if (e != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "cudaMalloc(plan tables)");
   }
-  if ((e = cudaMemcpy(p->d_lc, lc.data(), nlc * sizeof(pm::LimbConst), cudaMemcpyHostToDevice)) !=
-          cudaSuccess ||
-      (e = cudaMemcpy(p->d_twf, twf.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(p->d_twi, twi.data(), tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
+  if ((e = cudaMemcpy(d_lc, h_lc, lc_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d_twf, h_twf, tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(d_twi, h_twi, tw_bytes, cudaMemcpyHostToDevice)) != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "cudaMemcpy(plan tables)");
   }
@@ -421,7 +474,7 @@ pm_status pm_plan_reserve(pm_plan* plan, uint32_t npoly, void* stream) {
 }
 
 pm_status pm_ntt_fwd(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_ntt_fwd");
   if (s != PM_OK) return s;
   if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
   if ((s = check_batch(plan, npoly)) != PM_OK) return s;
@@ -436,7 +489,7 @@ pm_status pm_ntt_fwd(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* s
 }
 
 pm_status pm_ntt_inv(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_ntt_inv");
   if (s != PM_OK) return s;
   if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
   if ((s = check_batch(plan, npoly)) != PM_OK) return s;
@@ -452,7 +505,7 @@ pm_status pm_ntt_inv(const pm_plan* plan, uint64_t* d_x, uint32_t npoly, void* s
 
 pm_status pm_pointwise(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
                        uint64_t* d_c, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_pointwise");
   if (s != PM_OK) return s;
   if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
     return fail(PM_ERR_ARG, "NULL or misaligned pointer");
@@ -470,7 +523,7 @@ pm_status pm_pointwise(const pm_plan* plan, const uint64_t* d_a, const uint64_t*
 
 pm_status pm_polymul(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
                      uint64_t* d_c, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_polymul");
   if (s != PM_OK) return s;
   if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
     return fail(PM_ERR_ARG, "NULL or misaligned pointer");
@@ -525,7 +578,7 @@ extern "C" {
 
 pm_status pm_polymul_noalloc(const pm_plan* plan, const uint64_t* d_a, const uint64_t* d_b,
                              uint64_t* d_c, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_polymul_noalloc");
   if (s != PM_OK) return s;
   if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
     return fail(PM_ERR_ARG, "NULL or misaligned pointer");
@@ -554,7 +607,7 @@ pm_status pm_polymul_noalloc(const pm_plan* plan, const uint64_t* d_a, const uin
 pm_status pm_polymul_host(const pm_plan* plan, const uint64_t* h_a, const uint64_t* h_b,
                           uint64_t* h_c, uint64_t* d_a, uint64_t* d_b, uint64_t* d_c,
                           uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_polymul_host");
   if (s != PM_OK) return s;
   if (!h_a || !h_b || !h_c || !d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) ||
       !aligned16(d_c))
@@ -618,7 +671,7 @@ pm_status pm_polymul_host(const pm_plan* plan, const uint64_t* h_a, const uint64
 }
 
 pm_status pm_check_reduced(const pm_plan* plan, const uint64_t* d_x, uint32_t npoly, void* stream) {
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_check_reduced");
   if (s != PM_OK) return s;
   if (!d_x) return fail(PM_ERR_ARG, "d_x is NULL");
   if ((s = check_batch(plan, npoly)) != PM_OK) return s;
@@ -636,6 +689,96 @@ pm_status pm_check_reduced(const pm_plan* plan, const uint64_t* d_x, uint32_t np
       (e = cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_fail(e, "check_reduced");
+  if (flag) return fail(PM_ERR_RANGE, "a coefficient is >= its modulus");
+  return ok();
+}
+
+// ---- 32-bit words (PM_PLAN_WORD32): the same calls on uint32_t arrays.
+pm_status pm_ntt_fwd32(const pm_plan* plan, uint32_t* d_x, uint32_t npoly, void* stream) {
+  pm_status s = check_plan_word(plan, true, "pm_ntt_fwd32");
+  if (s != PM_OK) return s;
+  if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = reinterpret_cast<const uint64_t*>(d_x);
+  P.c = reinterpret_cast<uint64_t*>(d_x);
+  cudaError_t e = pm::launch_ntt_fwd(P, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ntt_fwd32 launch");
+  return ok();
+}
+
+pm_status pm_ntt_inv32(const pm_plan* plan, uint32_t* d_x, uint32_t npoly, void* stream) {
+  pm_status s = check_plan_word(plan, true, "pm_ntt_inv32");
+  if (s != PM_OK) return s;
+  if (!d_x || !aligned16(d_x)) return fail(PM_ERR_ARG, "d_x NULL or not 16-byte aligned");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = reinterpret_cast<const uint64_t*>(d_x);
+  P.c = reinterpret_cast<uint64_t*>(d_x);
+  cudaError_t e = pm::launch_ntt_inv(P, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ntt_inv32 launch");
+  return ok();
+}
+
+pm_status pm_pointwise32(const pm_plan* plan, const uint32_t* d_a, const uint32_t* d_b,
+                         uint32_t* d_c, uint32_t npoly, void* stream) {
+  pm_status s = check_plan_word(plan, true, "pm_pointwise32");
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm::KParams P = base_params(plan, npoly);
+  P.a = reinterpret_cast<const uint64_t*>(d_a);
+  P.b = reinterpret_cast<const uint64_t*>(d_b);
+  P.c = reinterpret_cast<uint64_t*>(d_c);
+  cudaError_t e = pm::launch_pointwise(P, (cudaStream_t)stream, plan->num_sms);
+  if (e != cudaSuccess) return cuda_fail(e, "pointwise32 launch");
+  return ok();
+}
+
+pm_status pm_polymul32(const pm_plan* plan, const uint32_t* d_a, const uint32_t* d_b,
+                       uint32_t* d_c, uint32_t npoly, void* stream) {
+  pm_status s = check_plan_word(plan, true, "pm_polymul32");
+  if (s != PM_OK) return s;
+  if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
+    return fail(PM_ERR_ARG, "NULL or misaligned pointer");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  s = polymul_impl(p, reinterpret_cast<const uint64_t*>(d_a),
+                   reinterpret_cast<const uint64_t*>(d_b), reinterpret_cast<uint64_t*>(d_c), npoly,
+                   (cudaStream_t)stream);
+  return s == PM_OK ? ok() : s;
+}
+
+pm_status pm_check_reduced32(const pm_plan* plan, const uint32_t* d_x, uint32_t npoly,
+                             void* stream) {
+  pm_status s = check_plan_word(plan, true, "pm_check_reduced32");
+  if (s != PM_OK) return s;
+  if (!d_x) return fail(PM_ERR_ARG, "d_x is NULL");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  DeviceGuard g(plan->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  pm_plan* p = const_cast<pm_plan*>(plan);
+  std::lock_guard<std::mutex> lk(p->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  pm::KParams P = base_params(p, npoly);
+  P.a = reinterpret_cast<const uint64_t*>(d_x);
+  int flag = 0;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(p->d_flag, 0, sizeof(int), st)) != cudaSuccess ||
+      (e = pm::launch_check_reduced(P, p->d_flag, st, p->num_sms)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&flag, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(e, "check_reduced32");
   if (flag) return fail(PM_ERR_RANGE, "a coefficient is >= its modulus");
   return ok();
 }
@@ -682,6 +825,8 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
     return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
   if (t->row_ops != 1 && t->row_ops != 2) return fail(PM_ERR_ARG, "row_ops must be 1 or 2");
+  if (t->variant == PM_VARIANT_PERSISTENT && is_word32(plan))
+    return fail(PM_ERR_ARG, "the persistent variant takes 64-bit plans");
   if (t->variant == PM_VARIANT_PERSISTENT &&
       (t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->lag_fwd < 1 || t->lag_inv <= t->lag_fwd ||
        t->lag_inv > 4096))
@@ -704,7 +849,7 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
   std::vector<pm_tuning> cand;
   cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
   if (plan->logn >= 12 && plan->logn != 13) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
-  if (plan->logn >= 13) {
+  if (plan->logn >= 13 && !is_word32(plan)) {
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});
   }
@@ -866,6 +1011,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
     if (J.plan->device != q->device)
       return fail(PM_ERR_ARG, "job %u: plan on device %d, queue on %d", j, J.plan->device, q->device);
+    if (is_word32(J.plan)) return fail(PM_ERR_ARG, "job %u: uneven batches take 64-bit plans", j);
     if (J.npoly == 0) return fail(PM_ERR_ARG, "job %u: npoly is 0", j);
     if (!J.a || !J.b || !J.c || !aligned16(J.a) || !aligned16(J.b) || !aligned16(J.c))
       return fail(PM_ERR_ARG, "job %u: NULL or misaligned pointer", j);
@@ -1065,7 +1211,7 @@ pm_status pm_graph_create_polymul(pm_graph** out, const pm_plan* plan, const uin
                                   const uint64_t* d_b, uint64_t* d_c, uint32_t npoly) {
   if (!out) return fail(PM_ERR_ARG, "out is NULL");
   *out = nullptr;
-  pm_status s = check_plan(plan);
+  pm_status s = check_plan_word(plan, false, "pm_graph_create_polymul");
   if (s != PM_OK) return s;
   if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
     return fail(PM_ERR_ARG, "NULL or misaligned pointer");
@@ -1451,6 +1597,7 @@ pm_status pm_server_submit(pm_server* S, const pm_plan* plan, const uint64_t* d_
   if (!S || !plan || !id_out) return fail(PM_ERR_ARG, "NULL argument");
   if (!d_a || !d_b || !aligned16(d_a) || !aligned16(d_b)) return fail(PM_ERR_ARG, "NULL or misaligned operand");
   if (plan->device != S->device) return fail(PM_ERR_ARG, "plan on another device");
+  if (is_word32(plan)) return fail(PM_ERR_ARG, "the server takes 64-bit plans");
   pm_status s = check_batch(plan, npoly);
   if (s != PM_OK) return s;
   const uint64_t need = ((uint64_t)npoly * plan->nlimbs << plan->logn << 3) +

@@ -27,6 +27,9 @@ struct KParams {
   uint32_t row_ops;      // polymul row kernel: 1 = operands one after the other, 2 = together
   uint32_t fused;        // polymul by Algorithm 8; lc then has 2 nlimbs entries, the second
                          // half (2/N in place of 1/N) used by the polymul launchers
+  uint32_t word32;       // 1: 32-bit words; a/b/c/s hold uint32_t, twf/twi TwPair32,
+                         // lc LimbConst32 (the pointers are reinterpreted)
+  uint32_t pad;
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the

@@ -31,6 +31,7 @@
 //   k_pointwise     : stand-alone Hadamard product with Algorithm 4.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "pm_arith.cuh"
 #include "pm_internal.h"
@@ -39,69 +40,126 @@
 namespace pm {
 
 // ------------------------------------------------------------------ kernels
+// Every kernel is a template over the word type W (W: q < 2^62;
+// uint32_t: q < 2^30); KParams carries untyped device pointers and KView<W>
+// gives the typed views.
+
+template <typename W>
+struct KView {
+  const W* a;
+  const W* b;
+  W* c;
+  W* s;
+  const typename WordT<W>::Tw* twf;
+  const typename WordT<W>::Tw* twi;
+  const typename WordT<W>::LC* lc;
+  __device__ __forceinline__ explicit KView(const KParams& P)
+      : a(reinterpret_cast<const W*>(P.a)),
+        b(reinterpret_cast<const W*>(P.b)),
+        c(reinterpret_cast<W*>(P.c)),
+        s(reinterpret_cast<W*>(P.s)),
+        twf(reinterpret_cast<const typename WordT<W>::Tw*>(P.twf)),
+        twi(reinterpret_cast<const typename WordT<W>::Tw*>(P.twi)),
+        lc(reinterpret_cast<const typename WordT<W>::LC*>(P.lc)) {}
+};
+
+// 16 consecutive words of a row (16-byte aligned) in or out with 16-byte
+// accesses; the store reduces [0, 4q) -> [0, q).
+template <typename W>
+__device__ __forceinline__ void ld_row16(W (&v)[16], const W* p) {
+  if constexpr (sizeof(W) == 8) {
+    const ulonglong2* s = reinterpret_cast<const ulonglong2*>(p);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const ulonglong2 w = __ldcs(s + k);
+      v[2 * k] = w.x;
+      v[2 * k + 1] = w.y;
+    }
+  } else {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint4 w = __ldcs(s + k);
+      v[4 * k] = w.x;
+      v[4 * k + 1] = w.y;
+      v[4 * k + 2] = w.z;
+      v[4 * k + 3] = w.w;
+    }
+  }
+}
+
+template <typename W>
+__device__ __forceinline__ void st_row16_reduced(W* p, const W (&v)[16], W q, W two_q) {
+  if constexpr (sizeof(W) == 8) {
+    ulonglong2* d = reinterpret_cast<ulonglong2*>(p);
+#pragma unroll
+    for (int k = 0; k < 8; k++)
+      __stcs(d + k, make_ulonglong2(reduce4(v[2 * k], q, two_q), reduce4(v[2 * k + 1], q, two_q)));
+  } else {
+    uint4* d = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+      __stcs(d + k, make_uint4(reduce4(v[4 * k], q, two_q), reduce4(v[4 * k + 1], q, two_q),
+                               reduce4(v[4 * k + 2], q, two_q), reduce4(v[4 * k + 3], q, two_q)));
+  }
+}
 
 // In-row stages for n >= 12.  One CTA = one row (256 threads).  For n == 12
 // the row is the whole unit (polymul reads a, b; output canonical).  For
 // n > 12, polymul reads the column-transformed operands from c and the
 // scratch s and leaves lazy c' rows for k_col_inv.
-template <int MODE, bool HALVE>
-__global__ void __launch_bounds__(256, 3) k_rows(KParams P) {
-  extern __shared__ __align__(16) uint64_t smem[];
+template <int MODE, bool HALVE, typename W>
+__global__ void __launch_bounds__(256, sizeof(W) == 8 ? 3 : 4) k_rows(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem_raw[];
+  W* smem = reinterpret_cast<W*>(smem_raw);
+  const KView<W> V(P);
   const uint32_t logn = P.logn;
   const uint32_t unit = blockIdx.x >> (logn - kRowLog);
   const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
   if (unit >= P.nunits) return;  // whole CTA exits together
   const uint32_t limb = unit % P.nlimbs;
-  const LimbConst K = ld_limb(P.lc + limb);
-  const TwPair* twf = P.twf + ((size_t)limb << logn);
-  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const auto K = ld_limb(V.lc + limb);
+  const auto* twf = V.twf + ((size_t)limb << logn);
+  const auto* twi = V.twi + ((size_t)limb << logn);
   const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
   const bool single = (logn == kRowLog);
   const int th = threadIdx.x;
-  uint64_t* sa = smem;
-  uint64_t* sb = smem + kRowPad;
-  uint64_t v[16];
+  W* sa = smem;
+  W* sb = smem + kRowPadW<W>;
+  W v[16];
   if constexpr (MODE == MODE_INV) {
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(P.c + off + 16 * th);
-#pragma unroll
-    for (int u = 0; u < 16; u += 2) {
-      const ulonglong2 w = __ldcs(src + u / 2);
-      v[u] = w.x;
-      v[u + 1] = w.y;
-    }
-    rows_inv<HALVE>(v, P.c + off, single, sa, twi, logn, t, th, K);
+    ld_row16(v, V.c + off + 16 * th);
+    rows_inv<HALVE>(v, V.c + off, single, sa, twi, logn, t, th, K);
   } else if constexpr (MODE == MODE_FWD) {
-    rows_fwd(v, P.c + off, sa, twf, logn, t, th, K.q, K.two_q);
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + off + 16 * th);
-#pragma unroll
-    for (int u = 0; u < 16; u += 2)
-      __stcs(dst + u / 2, make_ulonglong2(reduce4(v[u], K.q, K.two_q),
-                                          reduce4(v[u + 1], K.q, K.two_q)));
+    rows_fwd(v, V.c + off, sa, twf, logn, t, th, K.q, K.two_q);
+    st_row16_reduced(V.c + off + 16 * th, v, K.q, K.two_q);
   } else {
     (void)sb;
-    row_task_polymul<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
-                                   P.c + off, single, smem, twf, twi, K, logn, t,
+    row_task_polymul<HALVE, false>((single ? V.a : V.c) + off, (single ? V.b : V.s) + off,
+                                   V.c + off, single, smem, twf, twi, K, logn, t,
                                    MODE == MODE_POLYMUL_FUSED);
   }
 }
 
 // Polymul rows with a and b transformed together in registers (shared
 // twiddle loads, half the barriers per word; 2 CTAs per SM).
-template <bool HALVE, bool FUSED>
-__global__ void __launch_bounds__(256, 2) k_rows2(KParams P) {
-  extern __shared__ __align__(16) uint64_t smem[];
+template <bool HALVE, bool FUSED, typename W>
+__global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem_raw[];
+  W* smem = reinterpret_cast<W*>(smem_raw);
+  const KView<W> V(P);
   const uint32_t logn = P.logn;
   const uint32_t unit = blockIdx.x >> (logn - kRowLog);
   const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
   if (unit >= P.nunits) return;
   const uint32_t limb = unit % P.nlimbs;
-  const LimbConst K = ld_limb(P.lc + limb);
-  const TwPair* twf = P.twf + ((size_t)limb << logn);
-  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const auto K = ld_limb(V.lc + limb);
+  const auto* twf = V.twf + ((size_t)limb << logn);
+  const auto* twi = V.twi + ((size_t)limb << logn);
   const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
   const bool single = (logn == kRowLog);
-  row_task_polymul2<HALVE, false>((single ? P.a : P.c) + off, (single ? P.b : P.s) + off,
-                                  P.c + off, single, smem, twf, twi, K, logn, t, FUSED);
+  row_task_polymul2<HALVE, false>((single ? V.a : V.c) + off, (single ? V.b : V.s) + off,
+                                  V.c + off, single, smem, twf, twi, K, logn, t, FUSED);
 }
 
 // Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
@@ -111,36 +169,37 @@ __global__ void __launch_bounds__(256, 2) k_rows2(KParams P) {
 // Each thread walks S columns (stride = the grid's thread count) and loads
 // column k+1 while it transforms column k, so that its loads are in flight
 // during the arithmetic.
-template <int R, int S>
+template <int R, int S, typename W>
 __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+  const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * nops * kRow;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  uint64_t nx[R];
-  auto locate = [&](size_t id, const uint64_t*& src, uint64_t*& dst, uint32_t& limb) {
+  W nx[R];
+  auto locate = [&](size_t id, const W*& src, W*& dst, uint32_t& limb) {
     const uint32_t col = (uint32_t)(id & (kRow - 1));
     const size_t rest = id >> kRowLog;
     const uint32_t op = (uint32_t)(rest % nops);
     const uint32_t unit = (uint32_t)(rest / nops);
     limb = unit % P.nlimbs;
     const size_t off = ((size_t)unit << logn) + col;
-    src = (op == 0 ? P.a : P.b) + off;
-    dst = (op == 0 ? P.c : P.s) + off;
+    src = (op == 0 ? V.a : V.b) + off;
+    dst = (op == 0 ? V.c : V.s) + off;
   };
-  const uint64_t* src;
-  uint64_t* dst;
+  const W* src;
+  W* dst;
   uint32_t limb;
   locate(gid, src, dst, limb);
 #pragma unroll
   for (int t = 0; t < R; t++) nx[t] = __ldcs(src + (size_t)t * kRow);
 #pragma unroll 1
   for (int k = 0; k < S; k++) {
-    uint64_t x[R];
+    W x[R];
 #pragma unroll
     for (int t = 0; t < R; t++) x[t] = nx[t];
-    uint64_t* cur_dst = dst;
+    W* cur_dst = dst;
     const uint32_t cur_limb = limb;
     const size_t nid = gid + stride;
     const bool more = (k + 1 < S) && nid < total;
@@ -149,8 +208,8 @@ __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
 #pragma unroll
       for (int t = 0; t < R; t++) nx[t] = __ldcs(src + (size_t)t * kRow);
     }
-    const LimbConst K = ld_limb(P.lc + cur_limb);
-    ct_col<R>(x, P.twf + ((size_t)cur_limb << logn), K.q, K.two_q);
+    const auto K = ld_limb(V.lc + cur_limb);
+    ct_col<R>(x, V.twf + ((size_t)cur_limb << logn), K.q, K.two_q);
 #pragma unroll
     for (int t = 0; t < R; t++) cur_dst[(size_t)t * kRow] = x[t];
     if (!more) break;
@@ -161,31 +220,32 @@ __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
 // Inverse column stages (the last log2 R stages of Algorithm 7) plus the
 // reduction to [0, q); in place on c.  S columns per thread, software
 // pipelined as in k_col_fwd.
-template <int R, int S, bool HALVE>
+template <int R, int S, bool HALVE, typename W>
 __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
+  const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * kRow;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= total) return;
-  auto locate = [&](size_t id, uint64_t*& p, uint32_t& limb) {
+  auto locate = [&](size_t id, W*& p, uint32_t& limb) {
     const uint32_t col = (uint32_t)(id & (kRow - 1));
     const uint32_t unit = (uint32_t)(id >> kRowLog);
     limb = unit % P.nlimbs;
-    p = P.c + ((size_t)unit << logn) + col;
+    p = V.c + ((size_t)unit << logn) + col;
   };
-  uint64_t* p;
+  W* p;
   uint32_t limb;
   locate(gid, p, limb);
-  uint64_t nx[R];
+  W nx[R];
 #pragma unroll
   for (int t = 0; t < R; t++) nx[t] = p[(size_t)t * kRow];
 #pragma unroll 1
   for (int k = 0; k < S; k++) {
-    uint64_t x[R];
+    W x[R];
 #pragma unroll
     for (int t = 0; t < R; t++) x[t] = nx[t];
-    uint64_t* cur = p;
+    W* cur = p;
     const uint32_t cur_limb = limb;
     const size_t nid = gid + stride;
     const bool more = (k + 1 < S) && nid < total;
@@ -194,8 +254,8 @@ __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
 #pragma unroll
       for (int t = 0; t < R; t++) nx[t] = p[(size_t)t * kRow];
     }
-    const LimbConst K = ld_limb(P.lc + cur_limb);
-    gs_col<R, HALVE>(x, P.twi + ((size_t)cur_limb << logn), K);
+    const auto K = ld_limb(V.lc + cur_limb);
+    gs_col<R, HALVE>(x, V.twi + ((size_t)cur_limb << logn), K);
 #pragma unroll
     for (int t = 0; t < R; t++) __stcs(cur + (size_t)t * kRow, csub(x[t], K.q));
     if (!more) break;
@@ -205,80 +265,71 @@ __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
 
 // N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
 // (k = 4096) runs between global memory and smem; rows as in k_rows.
-template <int MODE, bool HALVE>
+template <int MODE, bool HALVE, typename W>
 __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
-  extern __shared__ __align__(16) uint64_t smem[];
+  extern __shared__ __align__(16) uint64_t smem_raw[];
+  W* smem = reinterpret_cast<W*>(smem_raw);
+  const KView<W> V(P);
   constexpr uint32_t logn = 13;
   const uint32_t unit = blockIdx.x;
   if (unit >= P.nunits) return;
   const uint32_t limb = unit % P.nlimbs;
-  const LimbConst K = ld_limb(P.lc + limb);
-  const TwPair* twf = P.twf + ((size_t)limb << logn);
-  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const auto K = ld_limb(V.lc + limb);
+  const auto* twf = V.twf + ((size_t)limb << logn);
+  const auto* twi = V.twi + ((size_t)limb << logn);
   const int tid = threadIdx.x;
   const int rho = tid >> 8, th = tid & 255;
   // smem: [a row0][a row1][b row0][b row1]
-  uint64_t* sA = smem;
-  uint64_t* sB = smem + 2 * kRowPad;
-  uint64_t* sa = sA + rho * kRowPad;
-  uint64_t* sb = sB + rho * kRowPad;
+  W* sA = smem;
+  W* sB = smem + 2 * kRowPadW<W>;
+  W* sa = sA + rho * kRowPadW<W>;
+  W* sb = sB + rho * kRowPadW<W>;
   const size_t base = (size_t)unit << logn;
-  uint64_t v[16];
+  W v[16];
   constexpr bool kFused = (MODE == MODE_POLYMUL_FUSED);
   if constexpr (MODE != MODE_INV) {
     const int nops = (MODE == MODE_FWD) ? 1 : 2;
-    const TwPair w = ld_tw(twf + 1);
+    const auto w = ld_tw(twf + 1);
     for (int op = 0; op < nops; op++) {
-      const uint64_t* src = (MODE == MODE_FWD) ? P.c + base : (op == 0 ? P.a : P.b) + base;
-      uint64_t* dsm = op == 0 ? sA : sB;
+      const W* src = (MODE == MODE_FWD) ? V.c + base : (op == 0 ? V.a : V.b) + base;
+      W* dsm = op == 0 ? sA : sB;
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         const int c = tid + 512 * k;
-        uint64_t x0 = __ldcs(src + c), x1 = __ldcs(src + kRow + c);
+        W x0 = __ldcs(src + c), x1 = __ldcs(src + kRow + c);
         ct_bfly(x0, x1, w.w, w.wp, K.q, K.two_q);
-        dsm[padj(c)] = x0;
-        dsm[kRowPad + padj(c)] = x1;
+        dsm[padj<W>(c)] = x0;
+        dsm[kRowPadW<W> + padj<W>(c)] = x1;
       }
     }
     __syncthreads();
     rows_fwd(v, nullptr, sa, twf, logn, rho, th, K.q, K.two_q, kFused);
     if constexpr (MODE == MODE_FWD) {
-      ulonglong2* dst = reinterpret_cast<ulonglong2*>(P.c + base + (size_t)rho * kRow + 16 * th);
-#pragma unroll
-      for (int u = 0; u < 16; u += 2)
-        __stcs(dst + u / 2, make_ulonglong2(reduce4(v[u], K.q, K.two_q),
-                                            reduce4(v[u + 1], K.q, K.two_q)));
+      st_row16_reduced(V.c + base + (size_t)rho * kRow + 16 * th, v, K.q, K.two_q);
       return;
     } else {
-      const PassGeo G2 = pass_geo(2, th, rho);
+      const PassGeo G2 = pass_geo<W>(2, th, rho);
       st_smem16(sa, G2, v);
       rows_fwd(v, nullptr, sb, twf, logn, rho, th, K.q, K.two_q, kFused);
-      const uint64_t* a2 = sa + G2.pbase;
+      const W* a2 = sa + G2.pbase;
       if constexpr (kFused)
         fused_pairs16_smem(v, a2, twf, logn, G2.g, K);
       else
         pointwise16(v, a2, K);
     }
   } else {
-    const ulonglong2* src =
-        reinterpret_cast<const ulonglong2*>(P.c + base + (size_t)rho * kRow + 16 * th);
-#pragma unroll
-    for (int u = 0; u < 16; u += 2) {
-      const ulonglong2 w = __ldcs(src + u / 2);
-      v[u] = w.x;
-      v[u + 1] = w.y;
-    }
+    ld_row16(v, V.c + base + (size_t)rho * kRow + 16 * th);
   }
   rows_inv<HALVE>(v, nullptr, false, sa, twi, logn, rho, th, K, kFused);
   __syncthreads();
   // last GS stage (k = 4096, twiddle Psi^-1_br[1]; 1/N folded in unless the
   // plan halves at every stage), then reduce
-  const TwPair w = ld_tw(twi + 1);
-  uint64_t* dst = P.c + base;
+  const auto w = ld_tw(twi + 1);
+  W* dst = V.c + base;
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     const int c = tid + 512 * k;
-    uint64_t x0 = sA[padj(c)], x1 = sA[kRowPad + padj(c)];
+    W x0 = sA[padj<W>(c)], x1 = sA[kRowPadW<W> + padj<W>(c)];
     if constexpr (HALVE)
       gs_bfly_half(x0, x1, w.w, w.wp, K.q, K.two_q, K.half_q1);
     else
@@ -289,20 +340,22 @@ __global__ void __launch_bounds__(512, 1) k_fused13(KParams P) {
 }
 
 // N <= 2^11: one CTA per unit, Algorithms 6 and 7 stage by stage in smem.
-template <int MODE, bool HALVE>
+template <int MODE, bool HALVE, typename W>
 __global__ void __launch_bounds__(256) k_small(KParams P) {
-  extern __shared__ __align__(16) uint64_t smem[];
+  extern __shared__ __align__(16) uint64_t smem_raw[];
+  W* smem = reinterpret_cast<W*>(smem_raw);
+  const KView<W> V(P);
   const uint32_t logn = P.logn, n = 1u << logn;
   const uint32_t unit = blockIdx.x;
   if (unit >= P.nunits) return;
   const uint32_t limb = unit % P.nlimbs;
-  const LimbConst K = ld_limb(P.lc + limb);
-  const TwPair* twf = P.twf + ((size_t)limb << logn);
-  const TwPair* twi = P.twi + ((size_t)limb << logn);
+  const auto K = ld_limb(V.lc + limb);
+  const auto* twf = V.twf + ((size_t)limb << logn);
+  const auto* twi = V.twi + ((size_t)limb << logn);
   const size_t base = (size_t)unit << logn;
-  uint64_t* xa = smem;
-  uint64_t* xb = smem + n;
-  const uint64_t q = K.q, two_q = K.two_q;
+  W* xa = smem;
+  W* xb = smem + n;
+  const W q = K.q, two_q = K.two_q;
   // Algorithm 8 (n >= 4): CT stops before its last stage (m = n/2), the pair
   // step replaces that stage, the products and the first GS stage, and GS
   // starts at m = n/4.
@@ -310,26 +363,26 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
   if constexpr (MODE != MODE_INV) {
     const int nops = (MODE == MODE_FWD) ? 1 : 2;
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      xa[i] = (MODE == MODE_FWD) ? P.c[base + i] : P.a[base + i];
-      if (nops == 2) xb[i] = P.b[base + i];
+      xa[i] = (MODE == MODE_FWD) ? V.c[base + i] : V.a[base + i];
+      if (nops == 2) xb[i] = V.b[base + i];
     }
     __syncthreads();
     for (uint32_t m = 1, k = n >> 1; m < (kFused ? n >> 1 : n); m <<= 1, k >>= 1) {
       for (uint32_t b = threadIdx.x; b < n / 2; b += blockDim.x) {
         const uint32_t i = b / k, j = 2 * i * k + (b % k);
-        const TwPair w = ld_tw(twf + m + i);
+        const auto w = ld_tw(twf + m + i);
         ct_bfly(xa[j], xa[j + k], w.w, w.wp, q, two_q);
         if (nops == 2) ct_bfly(xb[j], xb[j + k], w.w, w.wp, q, two_q);
       }
       __syncthreads();
     }
     if constexpr (MODE == MODE_FWD) {
-      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P.c[base + i] = reduce4(xa[i], q, two_q);
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) V.c[base + i] = reduce4(xa[i], q, two_q);
       return;
     }
     if constexpr (kFused) {
       for (uint32_t i = threadIdx.x; i < n / 2; i += blockDim.x) {
-        const TwPair w = ld_tw(twf + n / 4 + i / 2);
+        const auto w = ld_tw(twf + n / 4 + i / 2);
         if (i & 1)
           fused_pair<true>(xa[2 * i], xa[2 * i + 1], xb[2 * i], xb[2 * i + 1], w, K);
         else
@@ -340,7 +393,7 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
         xa[i] = mul_barrett_alg4(reduce4(xa[i], q, two_q), reduce4(xb[i], q, two_q), K);
     }
   } else {
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) xa[i] = P.c[base + i];
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) xa[i] = V.c[base + i];
   }
   __syncthreads();
   for (uint32_t m = n >> (kFused ? 2 : 1), k = kFused ? 2 : 1; m >= 1; m >>= 1, k <<= 1) {
@@ -349,47 +402,56 @@ __global__ void __launch_bounds__(256) k_small(KParams P) {
       if (!HALVE && m == 1) {
         gs_bfly_last(xa[j], xa[j + k], K);  // last stage: 1/N folded in
       } else {
-        const TwPair w = ld_tw(twi + m + i);
+        const auto w = ld_tw(twi + m + i);
         gs_bfly_mode<HALVE>(xa[j], xa[j + k], w.w, w.wp, q, two_q, K.half_q1);
       }
     }
     __syncthreads();
   }
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) P.c[base + i] = csub(xa[i], q);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) V.c[base + i] = csub(xa[i], q);
 }
 
 // Stand-alone pointwise product, Algorithm 4, two words per thread.
+template <typename W>
 __global__ void __launch_bounds__(256) k_pointwise(KParams P) {
+  const KView<W> V(P);
+  using V2 = typename std::conditional<sizeof(W) == 8, ulonglong2, uint2>::type;
   const size_t total = (size_t)P.nunits << P.logn;
   const size_t stride = (size_t)gridDim.x * blockDim.x * 2;
   for (size_t i = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < total; i += stride) {
     const uint32_t limb = (uint32_t)((i >> P.logn) % P.nlimbs);
-    const LimbConst K = ld_limb(P.lc + limb);
+    const auto K = ld_limb(V.lc + limb);
     if (i + 1 < total && ((i + 1) >> P.logn) == (i >> P.logn)) {
-      const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(P.a + i);
-      const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(P.b + i);
-      *reinterpret_cast<ulonglong2*>(P.c + i) =
-          make_ulonglong2(mul_barrett_alg4(a.x, b.x, K), mul_barrett_alg4(a.y, b.y, K));
+      const V2 a = *reinterpret_cast<const V2*>(V.a + i);
+      const V2 b = *reinterpret_cast<const V2*>(V.b + i);
+      V2 c;
+      c.x = mul_barrett_alg4(W(a.x), W(b.x), K);
+      c.y = mul_barrett_alg4(W(a.y), W(b.y), K);
+      *reinterpret_cast<V2*>(V.c + i) = c;
     } else {
       for (size_t k = i; k < i + 2 && k < total; k++) {
-        const LimbConst K2 = ld_limb(P.lc + (uint32_t)((k >> P.logn) % P.nlimbs));
-        P.c[k] = mul_barrett_alg4(P.a[k], P.b[k], K2);
+        const auto K2 = ld_limb(V.lc + (uint32_t)((k >> P.logn) % P.nlimbs));
+        V.c[k] = mul_barrett_alg4(V.a[k], V.b[k], K2);
       }
     }
   }
 }
 
 // Range check 0 <= x < q_l; sets *flag = 1 on any violation.
+template <typename W>
 __global__ void __launch_bounds__(256) k_check_reduced(KParams P, int* flag) {
+  const KView<W> V(P);
   const size_t total = (size_t)P.nunits << P.logn;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const uint32_t limb = (uint32_t)((i >> P.logn) % P.nlimbs);
-    if (P.a[i] >= __ldg(&P.lc[limb].q)) atomicOr(flag, 1);
+    if (V.a[i] >= __ldg(&V.lc[limb].q)) atomicOr(flag, 1);
   }
 }
 
 // ------------------------------------------------------------ launchers
+// Templates over the word type W; the entry points at the end dispatch on
+// KParams::word32.
 
 static cudaError_t set_smem(const void* fn, int bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -401,20 +463,20 @@ static cudaError_t set_smem(const void* fn, int bytes) {
 constexpr int kColsPerThread = 4;
 constexpr size_t kPipeMinCols = (size_t)1 << 20;
 
-template <int R>
+template <int R, typename W>
 static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
   const size_t cols = (size_t)P.nunits * nops * kRow;
   if (R < 32 && cols >= kPipeMinCols) {
     constexpr int S = kColsPerThread;
     const unsigned blocks = (unsigned)(((cols + S - 1) / S + 255) / 256);
-    k_col_fwd<R, S><<<blocks, 256, 0, st>>>(P, nops);
+    k_col_fwd<R, S, W><<<blocks, 256, 0, st>>>(P, nops);
   } else {
-    k_col_fwd<R, 1><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
+    k_col_fwd<R, 1, W><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
   }
   return cudaGetLastError();
 }
 
-template <int R>
+template <int R, typename W>
 static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
   const size_t cols = (size_t)P.nunits * kRow;
   const bool pipe = R < 32 && cols >= kPipeMinCols;
@@ -422,123 +484,139 @@ static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
   const unsigned blocks = (unsigned)((((pipe ? (cols + S - 1) / S : cols)) + 255) / 256);
   if (pipe) {
     if (P.halving)
-      k_col_inv<R, S, true><<<blocks, 256, 0, st>>>(P);
+      k_col_inv<R, S, true, W><<<blocks, 256, 0, st>>>(P);
     else
-      k_col_inv<R, S, false><<<blocks, 256, 0, st>>>(P);
+      k_col_inv<R, S, false, W><<<blocks, 256, 0, st>>>(P);
   } else {
     if (P.halving)
-      k_col_inv<R, 1, true><<<blocks, 256, 0, st>>>(P);
+      k_col_inv<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
     else
-      k_col_inv<R, 1, false><<<blocks, 256, 0, st>>>(P);
+      k_col_inv<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
   }
   return cudaGetLastError();
 }
 
+template <typename W>
 static cudaError_t col_fwd(const KParams& P, int nops, cudaStream_t st) {
   switch (P.logn) {
-    case 13: return launch_col_fwd<2>(P, nops, st);
-    case 14: return launch_col_fwd<4>(P, nops, st);
-    case 15: return launch_col_fwd<8>(P, nops, st);
-    case 16: return launch_col_fwd<16>(P, nops, st);
-    case 17: return launch_col_fwd<32>(P, nops, st);
+    case 13: return launch_col_fwd<2, W>(P, nops, st);
+    case 14: return launch_col_fwd<4, W>(P, nops, st);
+    case 15: return launch_col_fwd<8, W>(P, nops, st);
+    case 16: return launch_col_fwd<16, W>(P, nops, st);
+    case 17: return launch_col_fwd<32, W>(P, nops, st);
   }
   return cudaErrorInvalidValue;
 }
 
+template <typename W>
 static cudaError_t col_inv(const KParams& P, cudaStream_t st) {
   switch (P.logn) {
-    case 13: return launch_col_inv<2>(P, st);
-    case 14: return launch_col_inv<4>(P, st);
-    case 15: return launch_col_inv<8>(P, st);
-    case 16: return launch_col_inv<16>(P, st);
-    case 17: return launch_col_inv<32>(P, st);
+    case 13: return launch_col_inv<2, W>(P, st);
+    case 14: return launch_col_inv<4, W>(P, st);
+    case 15: return launch_col_inv<8, W>(P, st);
+    case 16: return launch_col_inv<16, W>(P, st);
+    case 17: return launch_col_inv<32, W>(P, st);
   }
   return cudaErrorInvalidValue;
 }
 
-constexpr int kRowsSmem = 2 * kRowPad * 8;
-constexpr int kFused13Smem = 4 * kRowPad * 8;
+template <typename W>
+constexpr int kRowsSmem = 2 * kRowPadW<W> * (int)sizeof(W);
+template <typename W>
+constexpr int kFused13Smem = 4 * kRowPadW<W> * (int)sizeof(W);
 
-template <int MODE>
+template <int MODE, typename W>
 static cudaError_t rows(const KParams& P, cudaStream_t st) {
   const unsigned blocks = P.nunits << (P.logn - kRowLog);
+  constexpr int smem = kRowsSmem<W>;
   if ((MODE == MODE_POLYMUL || MODE == MODE_POLYMUL_FUSED) && P.row_ops == 2) {
     constexpr bool F = (MODE == MODE_POLYMUL_FUSED);
     if (P.halving)
-      k_rows2<true, F><<<blocks, 256, kRowsSmem, st>>>(P);
+      k_rows2<true, F, W><<<blocks, 256, smem, st>>>(P);
     else
-      k_rows2<false, F><<<blocks, 256, kRowsSmem, st>>>(P);
+      k_rows2<false, F, W><<<blocks, 256, smem, st>>>(P);
     return cudaGetLastError();
   }
   if (P.halving)
-    k_rows<MODE, true><<<blocks, 256, kRowsSmem, st>>>(P);
+    k_rows<MODE, true, W><<<blocks, 256, smem, st>>>(P);
   else
-    k_rows<MODE, false><<<blocks, 256, kRowsSmem, st>>>(P);
+    k_rows<MODE, false, W><<<blocks, 256, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, typename W>
 static cudaError_t fused13(const KParams& P, cudaStream_t st) {
   if (P.halving)
-    k_fused13<MODE, true><<<P.nunits, 512, kFused13Smem, st>>>(P);
+    k_fused13<MODE, true, W><<<P.nunits, 512, kFused13Smem<W>, st>>>(P);
   else
-    k_fused13<MODE, false><<<P.nunits, 512, kFused13Smem, st>>>(P);
+    k_fused13<MODE, false, W><<<P.nunits, 512, kFused13Smem<W>, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, typename W>
 static cudaError_t small(const KParams& P, cudaStream_t st) {
-  const int smem = 2 * (1 << P.logn) * 8;
+  const int smem = 2 * (1 << P.logn) * (int)sizeof(W);
   if (P.halving)
-    k_small<MODE, true><<<P.nunits, 256, smem, st>>>(P);
+    k_small<MODE, true, W><<<P.nunits, 256, smem, st>>>(P);
   else
-    k_small<MODE, false><<<P.nunits, 256, smem, st>>>(P);
+    k_small<MODE, false, W><<<P.nunits, 256, smem, st>>>(P);
   return cudaGetLastError();
 }
 
-template <bool H>
+template <bool H, typename W>
 static cudaError_t prepare_mode() {
+  constexpr int rs = kRowsSmem<W>, fs = kFused13Smem<W>;
+  const void* rows_fns[] = {(const void*)k_rows<MODE_POLYMUL, H, W>,
+                            (const void*)k_rows<MODE_POLYMUL_FUSED, H, W>,
+                            (const void*)k_rows2<H, false, W>,
+                            (const void*)k_rows2<H, true, W>,
+                            (const void*)k_rows<MODE_FWD, H, W>,
+                            (const void*)k_rows<MODE_INV, H, W>};
+  const void* f13_fns[] = {(const void*)k_fused13<MODE_POLYMUL, H, W>,
+                           (const void*)k_fused13<MODE_POLYMUL_FUSED, H, W>,
+                           (const void*)k_fused13<MODE_FWD, H, W>,
+                           (const void*)k_fused13<MODE_INV, H, W>};
   cudaError_t e;
-  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL, H>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows<MODE_POLYMUL_FUSED, H>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows2<H, false>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows2<H, true>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows<MODE_FWD, H>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_rows<MODE_INV, H>, kRowsSmem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL, H>, kFused13Smem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_POLYMUL_FUSED, H>, kFused13Smem)) != cudaSuccess)
-    return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_FWD, H>, kFused13Smem)) != cudaSuccess) return e;
-  if ((e = set_smem((const void*)k_fused13<MODE_INV, H>, kFused13Smem)) != cudaSuccess) return e;
+  for (const void* f : rows_fns)
+    if ((e = set_smem(f, rs)) != cudaSuccess) return e;
+  for (const void* f : f13_fns)
+    if ((e = set_smem(f, fs)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
 // Opt the large-smem kernels in to their dynamic shared memory on the current
 // device (once per device, before the first launch).
 cudaError_t kernels_prepare() {
-  cudaError_t e = prepare_mode<false>();
-  return e != cudaSuccess ? e : prepare_mode<true>();
+  cudaError_t e;
+  if ((e = prepare_mode<false, uint64_t>()) != cudaSuccess) return e;
+  if ((e = prepare_mode<true, uint64_t>()) != cudaSuccess) return e;
+  if ((e = prepare_mode<false, uint32_t>()) != cudaSuccess) return e;
+  return prepare_mode<true, uint32_t>();
 }
 
 static inline cudaError_t mark(const PhaseEvents* pe, int k, cudaStream_t st) {
   return (pe && k < pe->n) ? cudaEventRecord(pe->ev[k], st) : cudaSuccess;
 }
 
-template <int MODE>
+template <int MODE, typename W>
 static cudaError_t polymul_rows(const KParams& P, cudaStream_t st) {
-  if (P.logn <= 11) return small<MODE>(P, st);
-  if (P.logn == 12) return rows<MODE>(P, st);
-  if (P.logn == 13) return fused13<MODE>(P, st);
-  return rows<MODE>(P, st);
+  if (P.logn <= 11) return small<MODE, W>(P, st);
+  if (P.logn == 12) return rows<MODE, W>(P, st);
+  if (P.logn == 13) return fused13<MODE, W>(P, st);
+  return rows<MODE, W>(P, st);
 }
 
-cudaError_t launch_polymul(const KParams& P0, cudaStream_t st, const PhaseEvents* pe) {
+template <typename W>
+static cudaError_t launch_polymul_w(const KParams& P0, cudaStream_t st, const PhaseEvents* pe) {
   KParams P = P0;
   if (P.nunits == 0) return cudaSuccess;
   // Algorithm 8 plans: the fused constants (2/N) follow the plain ones
-  if (P.fused) P.lc += P.nlimbs;
+  if (P.fused)
+    P.lc = reinterpret_cast<const LimbConst*>(
+        reinterpret_cast<const typename WordT<W>::LC*>(P.lc) + P.nlimbs);
   auto prows = [&](const KParams& Q) {
-    return Q.fused ? polymul_rows<MODE_POLYMUL_FUSED>(Q, st) : polymul_rows<MODE_POLYMUL>(Q, st);
+    return Q.fused ? polymul_rows<MODE_POLYMUL_FUSED, W>(Q, st)
+                   : polymul_rows<MODE_POLYMUL, W>(Q, st);
   };
   cudaError_t e0 = mark(pe, 0, st);
   if (e0 != cudaSuccess) return e0;
@@ -561,54 +639,75 @@ cudaError_t launch_polymul(const KParams& P0, cudaStream_t st, const PhaseEvents
     P.a = P.b;
     P.b = t;
   }
-  cudaError_t e = col_fwd(P, nops, st);
+  cudaError_t e = col_fwd<W>(P, nops, st);
   if (e == cudaSuccess) e = mark(pe, 1, st);
   if (e == cudaSuccess) e = prows(P);
   if (e == cudaSuccess) e = mark(pe, 2, st);
-  if (e == cudaSuccess) e = col_inv(P, st);
+  if (e == cudaSuccess) e = col_inv<W>(P, st);
   if (e == cudaSuccess) e = mark(pe, 3, st);
   return e;
 }
 
-cudaError_t launch_ntt_fwd(const KParams& P0, cudaStream_t st) {
+template <typename W>
+static cudaError_t launch_ntt_fwd_w(const KParams& P0, cudaStream_t st) {
   if (P0.nunits == 0) return cudaSuccess;
   KParams P = P0;
-  if (P.logn <= 11) return small<MODE_FWD>(P, st);
-  if (P.logn == 13) return fused13<MODE_FWD>(P, st);
+  if (P.logn <= 11) return small<MODE_FWD, W>(P, st);
+  if (P.logn == 13) return fused13<MODE_FWD, W>(P, st);
   if (P.logn > 13) {
     P.a = P.c;  // in place: column stages read and write x
-    cudaError_t e = col_fwd(P, 1, st);
+    cudaError_t e = col_fwd<W>(P, 1, st);
     if (e != cudaSuccess) return e;
   }
-  return rows<MODE_FWD>(P, st);
+  return rows<MODE_FWD, W>(P, st);
+}
+
+template <typename W>
+static cudaError_t launch_ntt_inv_w(const KParams& P, cudaStream_t st) {
+  if (P.nunits == 0) return cudaSuccess;
+  if (P.logn <= 11) return small<MODE_INV, W>(P, st);
+  if (P.logn == 13) return fused13<MODE_INV, W>(P, st);
+  cudaError_t e = rows<MODE_INV, W>(P, st);
+  if (e != cudaSuccess || P.logn == 12) return e;
+  return col_inv<W>(P, st);
+}
+
+static unsigned grid_cap(size_t blocks, int num_sms) {
+  const size_t cap = (size_t)num_sms * 8;
+  return (unsigned)(blocks > cap ? cap : blocks);
+}
+
+cudaError_t launch_polymul(const KParams& P, cudaStream_t st, const PhaseEvents* pe) {
+  return P.word32 ? launch_polymul_w<uint32_t>(P, st, pe) : launch_polymul_w<uint64_t>(P, st, pe);
+}
+
+cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st) {
+  return P.word32 ? launch_ntt_fwd_w<uint32_t>(P, st) : launch_ntt_fwd_w<uint64_t>(P, st);
 }
 
 cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st) {
-  if (P.nunits == 0) return cudaSuccess;
-  if (P.logn <= 11) return small<MODE_INV>(P, st);
-  if (P.logn == 13) return fused13<MODE_INV>(P, st);
-  cudaError_t e = rows<MODE_INV>(P, st);
-  if (e != cudaSuccess || P.logn == 12) return e;
-  return col_inv(P, st);
+  return P.word32 ? launch_ntt_inv_w<uint32_t>(P, st) : launch_ntt_inv_w<uint64_t>(P, st);
 }
 
 cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms) {
   const size_t total = (size_t)P.nunits << P.logn;
   if (total == 0) return cudaSuccess;
-  size_t blocks = (total / 2 + 255) / 256;
-  const size_t cap = (size_t)num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  k_pointwise<<<(unsigned)blocks, 256, 0, st>>>(P);
+  const unsigned blocks = grid_cap((total / 2 + 255) / 256, num_sms);
+  if (P.word32)
+    k_pointwise<uint32_t><<<blocks, 256, 0, st>>>(P);
+  else
+    k_pointwise<uint64_t><<<blocks, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st, int num_sms) {
   const size_t total = (size_t)P.nunits << P.logn;
   if (total == 0) return cudaSuccess;
-  size_t blocks = (total + 255) / 256;
-  const size_t cap = (size_t)num_sms * 8;
-  if (blocks > cap) blocks = cap;
-  k_check_reduced<<<(unsigned)blocks, 256, 0, st>>>(P, d_flag);
+  const unsigned blocks = grid_cap((total + 255) / 256, num_sms);
+  if (P.word32)
+    k_check_reduced<uint32_t><<<blocks, 256, 0, st>>>(P, d_flag);
+  else
+    k_check_reduced<uint64_t><<<blocks, 256, 0, st>>>(P, d_flag);
   return cudaGetLastError();
 }
 

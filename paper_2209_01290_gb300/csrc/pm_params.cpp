@@ -161,5 +161,55 @@ void fused_limb(const LimbConst& in, LimbConst* out) {
   out->w1ninv_p = shoup_companion(out->w1ninv, q);
 }
 
+// 32-bit words: the same tables with Shoup companions floor(w * 2^32 / q) and
+// Algorithm 4's mu = floor(2^(2m+1) / q) for beta = 32 (q < 2^30).
+void build_limb32(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbConst32* lc,
+                  TwPair32* twf, TwPair32* twi) {
+  const uint32_t n = 1u << log2n;
+  const uint32_t m = bit_length(q);
+  auto companion = [&](uint64_t w) { return (uint32_t)((w << 32) / q); };
+  lc->q = (uint32_t)q;
+  lc->two_q = (uint32_t)(2 * q);
+  lc->half_q1 = (uint32_t)((q + 1) / 2);
+  lc->mu = (uint32_t)((((u128)1) << (2 * m + 1)) / q);
+  lc->m = m;
+  lc->sh1 = m - 2;
+  lc->sh2 = m + 3;
+  lc->halving = halving ? 1 : 0;
+  const uint64_t psi_inv = pow_mod(psi, 2 * (uint64_t)n - 1, q);
+  const uint64_t inv2 = (q + 1) / 2;
+  std::vector<uint64_t> fw(n), iv(n);
+  fw[0] = 1;
+  iv[0] = 1;
+  for (uint32_t e = 1; e < n; ++e) {
+    fw[e] = mul_mod(fw[e - 1], psi, q);
+    iv[e] = mul_mod(iv[e - 1], psi_inv, q);
+  }
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t r = reverse_bits(i, log2n);
+    const uint64_t wf = fw[r];
+    const uint64_t wi = halving ? mul_mod(iv[r], inv2, q) : iv[r];
+    twf[i] = TwPair32{(uint32_t)wf, companion(wf)};
+    twi[i] = TwPair32{(uint32_t)wi, companion(wi)};
+  }
+  const uint64_t ninv = pow_mod(inv2, log2n, q);
+  const uint64_t w1 = n > 1 ? iv[reverse_bits(1, log2n)] : 1;
+  const uint64_t w1ninv = mul_mod(w1, ninv, q);
+  lc->ninv = (uint32_t)ninv;
+  lc->ninv_p = companion(ninv);
+  lc->w1ninv = (uint32_t)w1ninv;
+  lc->w1ninv_p = companion(w1ninv);
+}
+
+void fused_limb32(const LimbConst32& in, LimbConst32* out) {
+  *out = in;
+  const uint64_t q = in.q;
+  const uint64_t ninv = mul_mod(in.ninv, 2, q), w1ninv = mul_mod(in.w1ninv, 2, q);
+  out->ninv = (uint32_t)ninv;
+  out->ninv_p = (uint32_t)((ninv << 32) / q);
+  out->w1ninv = (uint32_t)w1ninv;
+  out->w1ninv_p = (uint32_t)((w1ninv << 32) / q);
+}
+
 }  // namespace host
 }  // namespace pm

@@ -24,6 +24,10 @@ void build_limb(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbCons
 // step already carries the 1/2 of the omitted first GS stage, so the scale
 // folded into the last stage becomes 2/N (N^-1 and Psi^-1_br[1] N^-1 times 2).
 void fused_limb(const LimbConst& in, LimbConst* out);
+// The same for 32-bit words (q < 2^30; companions floor(w * 2^32 / q)).
+void build_limb32(uint32_t log2n, uint64_t q, uint64_t psi, bool halving, LimbConst32* lc,
+                  TwPair32* twf, TwPair32* twi);
+void fused_limb32(const LimbConst32& in, LimbConst32* out);
 
 }  // namespace host
 }  // namespace pm

@@ -2,6 +2,8 @@
 // 2209.01290, Algorithms 6 and 7): radix-16 register groups of the merged CT
 // and GS transforms, column transforms, and the in-row pipeline that runs the
 // 12 in-row stages of a 4096-word row through padded shared memory.
+// Everything is a template over the word type W (uint64_t or uint32_t, see
+// pm_arith.cuh), deduced from the register arrays.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -13,15 +15,31 @@ namespace pm {
 
 constexpr int kRowLog = 12;
 constexpr int kRow = 1 << kRowLog;        // 4096 words per row
-// Two pad words after every 16 (p(j) = j + 2 floor(j/16)).  64-bit shared
-// accesses are served per half-warp and 128-bit ones per quarter-warp; with
-// this padding layouts 0 and 1 (64-bit, a half-warp reads 16 consecutive
-// words) and layout 2 (128-bit word pairs, quarter-warp chunks 9 th + u/2 are
-// distinct mod 8) are all free of bank conflicts, and every layout-2 pair
-// starts on a 16-byte boundary.
-constexpr int kRowPad = kRow + kRow / 8;
+// Pad words after every 16 words of a row: p(j) = j + P floor(j/16).
+// 64-bit words, P = 2: 64-bit shared accesses are served per half-warp and
+// 128-bit ones per quarter-warp; layouts 0 and 1 (64-bit, a half-warp reads 16
+// consecutive words) and layout 2 (128-bit word pairs, quarter-warp chunks
+// 9 th + u/2 are distinct mod 8) are all free of bank conflicts, and every
+// layout-2 pair starts on a 16-byte boundary.
+// 32-bit words, P = 1: accesses are served per warp (32 banks of 4 bytes);
+// layout 2 (17 th) and layout 1 (half-warps 16 banks apart) are conflict-free,
+// layout 0 has one 2-way conflict (lanes 0 and 31).
+template <typename W>
+constexpr int kPadW = sizeof(W) == 8 ? 2 : 1;
 
-__device__ __forceinline__ int padj(int j) { return j + 2 * (j >> 4); }
+// Non-deduced pointer parameter (so that nullptr can be passed for it).
+template <typename T>
+struct NoDeduce {
+  using type = T;
+};
+template <typename W>
+constexpr int kRowPadW = kRow + 256 * kPadW<W>;  // padded row length in words
+constexpr int kRowPad = kRowPadW<uint64_t>;
+
+template <typename W = uint64_t>
+__device__ __forceinline__ int padj(int j) {
+  return j + kPadW<W> * (j >> 4);
+}
 
 // ------------------------------------------------------------------ passes
 
@@ -30,19 +48,20 @@ __device__ __forceinline__ int padj(int j) { return j + 2 * (j >> 4); }
 // number g, its 16 words spaced N >> (s0+4) apart.  Stage s0+st pairs
 // (u, u + 8 >> st) with twiddle Psi_br[2^(s0+st) + g 2^st + (u >> (4-st))].
 // (Stages are template parameters so every register index is a constant.)
-template <int ST>
-__device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                            uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q) {
+template <int ST, typename W>
+__device__ __forceinline__ void ct16_stage1(W (&v)[16], const typename WordT<W>::Tw* __restrict__ tw,
+                                            uint32_t s0, uint32_t g, W q, W two_q) {
+  using Tw = typename WordT<W>::Tw;
   constexpr int h = 8 >> ST;
   const uint32_t base = (1u << (s0 + ST)) + (g << ST);  // even for ST >= 1
   if constexpr (ST == 0) {
-    const TwPair t = ld_tw(tw + base);
+    const Tw t = ld_tw(tw + base);
 #pragma unroll
     for (int u0 = 0; u0 < 8; u0++) ct_bfly(v[u0], v[u0 + 8], t.w, t.wp, q, two_q);
   } else {
 #pragma unroll
     for (int blk = 0; blk < (1 << ST); blk += 2) {
-      TwPair t[2];
+      Tw t[2];
       ld_tw2(tw + base + blk, t[0], t[1]);
 #pragma unroll
       for (int e = 0; e < 2; e++)
@@ -56,16 +75,16 @@ __device__ __forceinline__ void ct16_stage1(uint64_t (&v)[16], const TwPair* __r
 
 // The same four stages on two operands that share the twiddles (a and b of
 // one product): each twiddle pair is loaded once and used twice.
-template <int ST>
-__device__ __forceinline__ void ct16_stage2(uint64_t (&va)[16], uint64_t (&vb)[16],
-                                            const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
-                                            uint64_t q, uint64_t two_q) {
+template <int ST, typename W>
+__device__ __forceinline__ void ct16_stage2(W (&va)[16], W (&vb)[16],
+                                            const typename WordT<W>::Tw* __restrict__ tw,
+                                            uint32_t s0, uint32_t g, W q, W two_q) {
   constexpr int h = 8 >> ST;
   const uint32_t base = (1u << (s0 + ST)) + (g << ST);  // even for ST >= 1
   constexpr int nb = 1 << ST;
 #pragma unroll
   for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
-    TwPair t[2];
+    typename WordT<W>::Tw t[2];
     if constexpr (nb > 1)
       ld_tw2(tw + base + blk, t[0], t[1]);
     else
@@ -83,17 +102,19 @@ __device__ __forceinline__ void ct16_stage2(uint64_t (&va)[16], uint64_t (&vb)[1
 
 // skip_last omits the fourth stage: in the last pass of a forward transform
 // that is the transform's final stage, which Algorithm 8 leaves out.
-__device__ __forceinline__ void ct16_2(uint64_t (&va)[16], uint64_t (&vb)[16],
-                                       const TwPair* __restrict__ tw, uint32_t s0, uint32_t g,
-                                       uint64_t q, uint64_t two_q, bool skip_last = false) {
+template <typename W>
+__device__ __forceinline__ void ct16_2(W (&va)[16], W (&vb)[16],
+                                       const typename WordT<W>::Tw* __restrict__ tw, uint32_t s0,
+                                       uint32_t g, W q, W two_q, bool skip_last = false) {
   ct16_stage2<0>(va, vb, tw, s0, g, q, two_q);
   ct16_stage2<1>(va, vb, tw, s0, g, q, two_q);
   ct16_stage2<2>(va, vb, tw, s0, g, q, two_q);
   if (!skip_last) ct16_stage2<3>(va, vb, tw, s0, g, q, two_q);
 }
 
-__device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                     uint32_t s0, uint32_t g, uint64_t q, uint64_t two_q,
+template <typename W>
+__device__ __forceinline__ void ct16(W (&v)[16], const typename WordT<W>::Tw* __restrict__ tw,
+                                     uint32_t s0, uint32_t g, W q, W two_q,
                                      bool skip_last = false) {
   ct16_stage1<0>(v, tw, s0, g, q, two_q);
   ct16_stage1<1>(v, tw, s0, g, q, two_q);
@@ -105,10 +126,10 @@ __device__ __forceinline__ void ct16(uint64_t (&v)[16], const TwPair* __restrict
 // 16 words.  GS stages sig0..sig0+3 (k = 2^sig); the group is block g of
 // 2^(sig0+4) words.  Stage sig0+st pairs (u, u + 2^st) with twiddle
 // Psi^-1_br[(N >> (sig0+st+1)) + g 2^(3-st) + (u >> (st+1))] (times 1/2).
-template <int ST, bool HALVE>
-__device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                           uint32_t logn, uint32_t sig0, uint32_t g,
-                                           uint64_t q, uint64_t two_q, uint64_t hq) {
+template <int ST, bool HALVE, typename W>
+__device__ __forceinline__ void gs16_stage(W (&v)[16], const typename WordT<W>::Tw* __restrict__ tw,
+                                           uint32_t logn, uint32_t sig0, uint32_t g, W q,
+                                           W two_q, W hq) {
   constexpr int h = 1 << ST;
   // base is even whenever the stage needs more than one twiddle (ST <= 2):
   // logn - sig0 - ST - 1 >= 1 there, and g << (3 - ST) is even
@@ -116,7 +137,7 @@ __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __re
   constexpr int nb = 8 >> ST;
 #pragma unroll
   for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
-    TwPair t[2];
+    typename WordT<W>::Tw t[2];
     if constexpr (nb > 1)
       ld_tw2(tw + base + blk, t[0], t[1]);
     else
@@ -132,11 +153,10 @@ __device__ __forceinline__ void gs16_stage(uint64_t (&v)[16], const TwPair* __re
 
 // skip_first omits the first stage (the transform's first when sig0 = 0,
 // which Algorithm 8 leaves out).
-template <bool HALVE>
-__device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict__ tw,
-                                     uint32_t logn, uint32_t sig0, uint32_t g,
-                                     uint64_t q, uint64_t two_q, uint64_t hq,
-                                     bool skip_first = false) {
+template <bool HALVE, typename W>
+__device__ __forceinline__ void gs16(W (&v)[16], const typename WordT<W>::Tw* __restrict__ tw,
+                                     uint32_t logn, uint32_t sig0, uint32_t g, W q, W two_q,
+                                     W hq, bool skip_first = false) {
   if (!skip_first) gs16_stage<0, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
   gs16_stage<1, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
   gs16_stage<2, HALVE>(v, tw, logn, sig0, g, q, two_q, hq);
@@ -145,15 +165,15 @@ __device__ __forceinline__ void gs16(uint64_t (&v)[16], const TwPair* __restrict
 
 // Merged CT on a column of R words (the first log2 R stages of the N-point
 // transform): stage s pairs (t, t + R >> (s+1)) with twiddle Psi_br[2^s + blk].
-template <int R, int S>
-__device__ __forceinline__ void ct_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                             uint64_t q, uint64_t two_q) {
+template <int R, int S, typename W>
+__device__ __forceinline__ void ct_col_stage(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
+                                             W q, W two_q) {
   if constexpr ((1 << S) < R) {
     constexpr int h = R >> (S + 1);
     constexpr int nb = 1 << S;
 #pragma unroll
     for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
-      TwPair t[2];
+      typename WordT<W>::Tw t[2];
       if constexpr (nb > 1)
         ld_tw2(tw + nb + blk, t[0], t[1]);  // index nb + blk is even
       else
@@ -169,9 +189,9 @@ __device__ __forceinline__ void ct_col_stage(uint64_t (&x)[R], const TwPair* __r
   }
 }
 
-template <int R>
-__device__ __forceinline__ void ct_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                       uint64_t q, uint64_t two_q) {
+template <int R, typename W>
+__device__ __forceinline__ void ct_col(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
+                                       W q, W two_q) {
   ct_col_stage<R, 0>(x, tw, q, two_q);
 }
 
@@ -179,9 +199,9 @@ __device__ __forceinline__ void ct_col(uint64_t (&x)[R], const TwPair* __restric
 // with k = 4096 * 2^E pairs (t, t + 2^E) with twiddle
 // Psi^-1_br[(R >> (E+1)) + (t >> (E+1))].  Without per-stage halving the
 // final stage (2^E = R/2, the transform's last) folds in 1/N.
-template <int R, int E, bool HALVE>
-__device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                             const LimbConst& K) {
+template <int R, int E, bool HALVE, typename W>
+__device__ __forceinline__ void gs_col_stage(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
+                                             const typename WordT<W>::LC& K) {
   if constexpr ((1 << E) < R) {
     constexpr int h = 1 << E;
     if constexpr (!HALVE && 2 * h == R) {
@@ -191,7 +211,7 @@ __device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __r
       constexpr int nb = R / (2 * h);  // table index nb + blk, even when nb > 1
 #pragma unroll
       for (int blk = 0; blk < nb; blk += (nb > 1 ? 2 : 1)) {
-        TwPair t[2];
+        typename WordT<W>::Tw t[2];
         if constexpr (nb > 1)
           ld_tw2(tw + nb + blk, t[0], t[1]);
         else
@@ -208,9 +228,9 @@ __device__ __forceinline__ void gs_col_stage(uint64_t (&x)[R], const TwPair* __r
   }
 }
 
-template <int R, bool HALVE>
-__device__ __forceinline__ void gs_col(uint64_t (&x)[R], const TwPair* __restrict__ tw,
-                                       const LimbConst& K) {
+template <int R, bool HALVE, typename W>
+__device__ __forceinline__ void gs_col(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
+                                       const typename WordT<W>::LC& K) {
   gs_col_stage<R, 0, HALVE>(x, tw, K);
 }
 
@@ -234,6 +254,25 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
   return k;
 }
 
+__device__ __forceinline__ LimbConst32 ld_limb(const LimbConst32* __restrict__ p) {
+  LimbConst32 k;
+  const uint4* s = reinterpret_cast<const uint4*>(p);
+  const uint4 v0 = __ldg(s), v1 = __ldg(s + 1), v2 = __ldg(s + 2);
+  k.q = v0.x;
+  k.two_q = v0.y;
+  k.half_q1 = v0.z;
+  k.mu = v0.w;
+  k.m = v1.x;
+  k.sh1 = v1.y;
+  k.sh2 = v1.z;
+  k.halving = v1.w;
+  k.ninv = v2.x;
+  k.ninv_p = v2.y;
+  k.w1ninv = v2.z;
+  k.w1ninv_p = v2.w;
+  return k;
+}
+
 // ----------------------------------------------------------- row pipeline
 
 // The 12 in-row stages of one 4096-word row (row t of a unit of 2^logn
@@ -243,43 +282,47 @@ __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
 //   layout 0: j = th + 256 u                      (CT stages n-12.., GS 8..11)
 //   layout 1: j = 256 (th>>4) + (th&15) + 16 u    (CT stages n-8..,  GS 4..7)
 //   layout 2: j = 16 th + u                       (CT stages n-4..,  GS 0..3)
-// are all bank-conflict free with the 1-in-16 padding.  The pass loop is
-// not unrolled: one copy of the radix-16 body serves all passes, which keeps
-// the kernel small enough for the instruction cache.
+// use the padding described at kPadW.  The pass loop of the one-operand
+// transforms is not unrolled: one copy of the radix-16 body serves all
+// passes, which keeps the kernel small enough for the instruction cache.
 struct PassGeo {
   int layout;    // 0, 1 or 2
   int pbase;     // padded smem index of u = 0
   uint32_t g;    // block index of the group within the whole transform
 };
 
-// With the padding p(j) = j + 2 floor(j/16), the padded index of word u of a
+// With the padding p(j) = j + P floor(j/16), the padded index of word u of a
 // group is pbase + off(u) with a compile-time offset per layout:
-//   layout 0: 288 u;  layout 1: 18 u;  layout 2: u.
-template <int L>
+//   layout 0: (256 + 16 P) u;  layout 1: (16 + P) u;  layout 2: u.
+template <int L, typename W>
 __device__ __forceinline__ constexpr int lay_off(int u) {
-  return L == 0 ? 288 * u : (L == 1 ? 18 * u : u);
+  constexpr int P = kPadW<W>;
+  return L == 0 ? (256 + 16 * P) * u : (L == 1 ? (16 + P) * u : u);
 }
 
+template <typename W = uint64_t>
 __device__ __forceinline__ PassGeo pass_geo(int layout, int th, uint32_t t) {
+  constexpr int P = kPadW<W>;
   PassGeo G;
   G.layout = layout;
   if (layout == 0) {
-    G.pbase = th + 2 * (th >> 4);
+    G.pbase = th + P * (th >> 4);
     G.g = t;
   } else if (layout == 1) {
-    G.pbase = 288 * (th >> 4) + (th & 15);
+    G.pbase = (256 + 16 * P) * (th >> 4) + (th & 15);
     G.g = t * 16 + (th >> 4);
   } else {
-    G.pbase = 18 * th;
+    G.pbase = (16 + P) * th;
     G.g = t * 256 + th;
   }
   return G;
 }
 
-// Layout 2 moves its 16 consecutive words as 8 16-byte pairs.
-template <int L>
-__device__ __forceinline__ void ld16(uint64_t (&v)[16], const uint64_t* s) {
-  if constexpr (L == 2) {
+// With 64-bit words, layout 2 moves its 16 consecutive words as 8 16-byte
+// pairs; 32-bit words move one by one.
+template <int L, typename W>
+__device__ __forceinline__ void ld16(W (&v)[16], const W* s) {
+  if constexpr (L == 2 && sizeof(W) == 8) {
     const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(s);
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -289,31 +332,33 @@ __device__ __forceinline__ void ld16(uint64_t (&v)[16], const uint64_t* s) {
     }
   } else {
 #pragma unroll
-    for (int u = 0; u < 16; u++) v[u] = s[lay_off<L>(u)];
+    for (int u = 0; u < 16; u++) v[u] = s[lay_off<L, W>(u)];
   }
 }
 
-template <int L>
-__device__ __forceinline__ void st16(uint64_t* s, const uint64_t (&v)[16]) {
-  if constexpr (L == 2) {
+template <int L, typename W>
+__device__ __forceinline__ void st16(W* s, const W (&v)[16]) {
+  if constexpr (L == 2 && sizeof(W) == 8) {
     ulonglong2* s2 = reinterpret_cast<ulonglong2*>(s);
 #pragma unroll
     for (int k = 0; k < 8; k++) s2[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
   } else {
 #pragma unroll
-    for (int u = 0; u < 16; u++) s[lay_off<L>(u)] = v[u];
+    for (int u = 0; u < 16; u++) s[lay_off<L, W>(u)] = v[u];
   }
 }
 
-__device__ __forceinline__ void ld_smem16(uint64_t (&v)[16], const uint64_t* s, const PassGeo& G) {
-  const uint64_t* p = s + G.pbase;
+template <typename W>
+__device__ __forceinline__ void ld_smem16(W (&v)[16], const W* s, const PassGeo& G) {
+  const W* p = s + G.pbase;
   if (G.layout == 0) ld16<0>(v, p);
   else if (G.layout == 1) ld16<1>(v, p);
   else ld16<2>(v, p);
 }
 
-__device__ __forceinline__ void st_smem16(uint64_t* s, const PassGeo& G, const uint64_t (&v)[16]) {
-  uint64_t* p = s + G.pbase;
+template <typename W>
+__device__ __forceinline__ void st_smem16(W* s, const PassGeo& G, const W (&v)[16]) {
+  W* p = s + G.pbase;
   if (G.layout == 0) st16<0>(p, v);
   else if (G.layout == 1) st16<1>(p, v);
   else st16<2>(p, v);
@@ -322,8 +367,8 @@ __device__ __forceinline__ void st_smem16(uint64_t* s, const PassGeo& G, const u
 // Global loads of data written earlier in the same launch (persistent
 // kernel) must bypass L1: CG selects ld.global.cg, otherwise the streaming
 // ld.global.cs hint is used.
-template <bool CG>
-__device__ __forceinline__ uint64_t ld_g(const uint64_t* p) {
+template <bool CG, typename W>
+__device__ __forceinline__ W ld_g(const W* p) {
   if constexpr (CG)
     return __ldcg(p);
   else
@@ -335,14 +380,14 @@ __device__ __forceinline__ uint64_t ld_g(const uint64_t* p) {
 // Leaves the last pass's 16 words (layout 2, lazy [0,4q)) in v.
 // With `trunc` the transform's final stage is omitted (Algorithm 8's
 // truncated CT transform).
-template <bool CG = false>
-__device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_src, uint64_t* s,
-                                         const TwPair* __restrict__ twf, uint32_t logn,
-                                         uint32_t t, int th, uint64_t q, uint64_t two_q,
+template <bool CG = false, typename W>
+__device__ __forceinline__ void rows_fwd(W (&v)[16], const typename NoDeduce<W>::type* g_src, W* s,
+                                         const typename WordT<W>::Tw* __restrict__ twf,
+                                         uint32_t logn, uint32_t t, int th, W q, W two_q,
                                          bool trunc = false) {
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
-    const PassGeo G = pass_geo(p, th, t);
+    const PassGeo G = pass_geo<W>(p, th, t);
     if (p == 0 && g_src) {
 #pragma unroll
       for (int u = 0; u < 16; u++) v[u] = ld_g<CG>(g_src + th + 256 * u);
@@ -370,15 +415,16 @@ __device__ __forceinline__ void rows_fwd(uint64_t (&v)[16], const uint64_t* g_sr
 // halving, the outputs are multiplied by N^-1 (K.ninv) before the store.
 // With `trunc` the transform's first stage is omitted (Algorithm 8's
 // truncated GS transform).
-template <bool HALVE>
-__device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, bool final,
-                                         uint64_t* s, const TwPair* __restrict__ twi,
-                                         uint32_t logn, uint32_t t, int th, const LimbConst& K,
-                                         bool trunc = false) {
-  const uint64_t q = K.q, two_q = K.two_q, hq = K.half_q1;
+template <bool HALVE, typename W>
+__device__ __forceinline__ void rows_inv(W (&v)[16], typename NoDeduce<W>::type* g_dst, bool final,
+                                         W* s,
+                                         const typename WordT<W>::Tw* __restrict__ twi,
+                                         uint32_t logn, uint32_t t, int th,
+                                         const typename WordT<W>::LC& K, bool trunc = false) {
+  const W q = K.q, two_q = K.two_q, hq = K.half_q1;
 #pragma unroll 1
   for (int p = 0; p < 3; p++) {
-    const PassGeo G = pass_geo(2 - p, th, t);
+    const PassGeo G = pass_geo<W>(2 - p, th, t);
     if (p > 0) ld_smem16(v, s, G);
     gs16<HALVE>(v, twi, logn, 4 * p, G.g, q, two_q, hq, trunc && p == 0);
     if (p < 2) {
@@ -398,25 +444,25 @@ __device__ __forceinline__ void rows_inv(uint64_t (&v)[16], uint64_t* g_dst, boo
 #pragma unroll
     for (int u = 0; u < 16; u++) __stcs(g_dst + th + 256 * u, final ? csub(v[u], q) : v[u]);
   } else {
-    st_smem16(s, pass_geo(0, th, t), v);
+    st_smem16(s, pass_geo<W>(0, th, t), v);
   }
 }
 
 
 // Forward in-row stages of a and b together (shared twiddles); leaves the
 // layout-2 words of both in va, vb.
-template <bool CG = false>
-__device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16],
-                                          const uint64_t* ga, const uint64_t* gb, uint64_t* sa,
-                                          uint64_t* sb, const TwPair* __restrict__ twf,
-                                          uint32_t logn, uint32_t t, int th, uint64_t q,
-                                          uint64_t two_q, bool trunc = false) {
+template <bool CG = false, typename W>
+__device__ __forceinline__ void rows_fwd2(W (&va)[16], W (&vb)[16], const W* ga, const W* gb,
+                                          W* sa, W* sb,
+                                          const typename WordT<W>::Tw* __restrict__ twf,
+                                          uint32_t logn, uint32_t t, int th, W q, W two_q,
+                                          bool trunc = false) {
   // unrolled: with the layout of every pass known at compile time the
   // scheduler interleaves the two operands' loads and butterflies across
   // the pass (measured faster than the rolled loop here, unlike rows_fwd)
 #pragma unroll
   for (int p = 0; p < 3; p++) {
-    const PassGeo G = pass_geo(p, th, t);
+    const PassGeo G = pass_geo<W>(p, th, t);
     if (p == 0) {
 #pragma unroll
       for (int u = 0; u < 16; u++) {
@@ -447,18 +493,19 @@ __device__ __forceinline__ void rows_fwd2(uint64_t (&va)[16], uint64_t (&vb)[16]
 // with three Algorithm 4 products and one Shoup product by Psi_br[..]; the
 // sign (-1)^i is a compile-time choice between u + z and u - z.  This is the
 // first GS stage's output with its 1/2, in [0, 2q).
-template <bool ODD>
-__device__ __forceinline__ void fused_pair(uint64_t& x0, uint64_t& x1, uint64_t y0, uint64_t y1,
-                                           const TwPair& w, const LimbConst& K) {
-  const uint64_t q = K.q, two_q = K.two_q;
-  const uint64_t a0 = reduce4(x0, q, two_q), a1 = reduce4(x1, q, two_q);
-  const uint64_t b0 = reduce4(y0, q, two_q), b1 = reduce4(y1, q, two_q);
-  const uint64_t u = mul_barrett_alg4(a0, b0, K);                               // [0, q)
-  const uint64_t v = mul_barrett_alg4(a1, b1, K);                               // [0, q)
-  const uint64_t w3 = mul_barrett_alg4(csub(a0 + a1, q), csub(b0 + b1, q), K);  // [0, q)
-  const uint64_t z = mul_shoup_lazy(v, w.w, w.wp, q);                           // [0, 2q)
-  x1 = csub(w3 + two_q - u - v, two_q);                                         // (0,3q) -> [0,2q)
-  x0 = csub(ODD ? u + two_q - z : u + z, two_q);                                // [0,3q) -> [0,2q)
+template <bool ODD, typename W>
+__device__ __forceinline__ void fused_pair(W& x0, W& x1, W y0, W y1,
+                                           const typename WordT<W>::Tw& w,
+                                           const typename WordT<W>::LC& K) {
+  const W q = K.q, two_q = K.two_q;
+  const W a0 = reduce4(x0, q, two_q), a1 = reduce4(x1, q, two_q);
+  const W b0 = reduce4(y0, q, two_q), b1 = reduce4(y1, q, two_q);
+  const W u = mul_barrett_alg4(a0, b0, K);                                      // [0, q)
+  const W v = mul_barrett_alg4(a1, b1, K);                                      // [0, q)
+  const W w3 = mul_barrett_alg4(csub(W(a0 + a1), q), csub(W(b0 + b1), q), K);  // [0, q)
+  const W z = mul_shoup_lazy(v, w.w, w.wp, q);                                  // [0, 2q)
+  x1 = csub(W(w3 + two_q - u - v), two_q);                                      // (0,3q) -> [0,2q)
+  x0 = csub(W(ODD ? u + two_q - z : u + z), two_q);                             // [0,3q) -> [0,2q)
 }
 
 // The fused step on the 8 pairs (u, u+1) of a layout-2 register group (group
@@ -467,13 +514,15 @@ __device__ __forceinline__ void fused_pair(uint64_t& x0, uint64_t& x1, uint64_t 
 // step is symmetric in the two operands; the other operand comes from
 // registers (vb) or from its layout-2 words in shared memory (sb, 16-byte
 // pairs).
-__device__ __forceinline__ void fused_pairs16(uint64_t (&va)[16], const uint64_t (&vb)[16],
-                                              const TwPair* __restrict__ twf, uint32_t logn,
-                                              uint32_t g, const LimbConst& K) {
+template <typename W>
+__device__ __forceinline__ void fused_pairs16(W (&va)[16], const W (&vb)[16],
+                                              const typename WordT<W>::Tw* __restrict__ twf,
+                                              uint32_t logn, uint32_t g,
+                                              const typename WordT<W>::LC& K) {
   const uint32_t base = (1u << (logn - 2)) + 4 * g;  // even
 #pragma unroll
   for (int k = 0; k < 4; k += 2) {
-    TwPair w[2];
+    typename WordT<W>::Tw w[2];
     ld_tw2(twf + base + k, w[0], w[1]);
 #pragma unroll
     for (int e = 0; e < 2; e++) {
@@ -484,44 +533,66 @@ __device__ __forceinline__ void fused_pairs16(uint64_t (&va)[16], const uint64_t
   }
 }
 
-__device__ __forceinline__ void fused_pairs16_smem(uint64_t (&va)[16], const uint64_t* sb,
-                                                   const TwPair* __restrict__ twf,
-                                                   uint32_t logn, uint32_t g, const LimbConst& K) {
-  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+template <typename W>
+__device__ __forceinline__ void fused_pairs16_smem(W (&va)[16], const W* sb,
+                                                   const typename WordT<W>::Tw* __restrict__ twf,
+                                                   uint32_t logn, uint32_t g,
+                                                   const typename WordT<W>::LC& K) {
   const uint32_t base = (1u << (logn - 2)) + 4 * g;  // even
 #pragma unroll
   for (int k = 0; k < 4; k += 2) {
-    TwPair w[2];
+    typename WordT<W>::Tw w[2];
     ld_tw2(twf + base + k, w[0], w[1]);
 #pragma unroll
     for (int e = 0; e < 2; e++) {
       const int u = 4 * (k + e);
-      const ulonglong2 y0 = s2[u / 2], y1 = s2[u / 2 + 1];
-      fused_pair<false>(va[u], va[u + 1], y0.x, y0.y, w[e], K);
-      fused_pair<true>(va[u + 2], va[u + 3], y1.x, y1.y, w[e], K);
+      W y[4];
+      if constexpr (sizeof(W) == 8) {
+        const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+        const ulonglong2 p0 = s2[u / 2], p1 = s2[u / 2 + 1];
+        y[0] = p0.x;
+        y[1] = p0.y;
+        y[2] = p1.x;
+        y[3] = p1.y;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) y[i] = sb[u + i];
+      }
+      fused_pair<false>(va[u], va[u + 1], y[0], y[1], w[e], K);
+      fused_pair<true>(va[u + 2], va[u + 3], y[2], y[3], w[e], K);
     }
   }
 }
 
 // Algorithm 4 products of a register group with the other operand's
 // layout-2 words in shared memory (16-byte pairs).
-__device__ __forceinline__ void pointwise16(uint64_t (&v)[16], const uint64_t* sb,
-                                            const LimbConst& K) {
-  const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sb);
+template <typename W>
+__device__ __forceinline__ void pointwise16(W (&v)[16], const W* sb,
+                                            const typename WordT<W>::LC& K) {
 #pragma unroll
   for (int k = 0; k < 8; k++) {
-    const ulonglong2 y = s2[k];
-    v[2 * k] = mul_barrett_alg4(reduce4(y.x, K.q, K.two_q), reduce4(v[2 * k], K.q, K.two_q), K);
+    W y0, y1;
+    if constexpr (sizeof(W) == 8) {
+      const ulonglong2 y = reinterpret_cast<const ulonglong2*>(sb)[k];
+      y0 = y.x;
+      y1 = y.y;
+    } else {
+      y0 = sb[2 * k];
+      y1 = sb[2 * k + 1];
+    }
+    v[2 * k] = mul_barrett_alg4(reduce4(y0, K.q, K.two_q), reduce4(v[2 * k], K.q, K.two_q), K);
     v[2 * k + 1] =
-        mul_barrett_alg4(reduce4(y.y, K.q, K.two_q), reduce4(v[2 * k + 1], K.q, K.two_q), K);
+        mul_barrett_alg4(reduce4(y1, K.q, K.two_q), reduce4(v[2 * k + 1], K.q, K.two_q), K);
   }
 }
 
 // The product step between the forward and inverse in-row stages: Algorithm
 // 4 pointwise products (Eq. 2) or, with `fused`, Algorithm 8's pair step.
-__device__ __forceinline__ void row_product(uint64_t (&va)[16], const uint64_t (&vb)[16],
-                                            bool fused, const TwPair* __restrict__ twf,
-                                            uint32_t logn, uint32_t g, const LimbConst& K) {
+template <typename W>
+__device__ __forceinline__ void row_product(W (&va)[16], const W (&vb)[16], bool fused,
+                                            const typename WordT<W>::Tw* __restrict__ twf,
+                                            uint32_t logn, uint32_t g,
+                                            const typename WordT<W>::LC& K) {
   if (fused) {
     fused_pairs16(va, vb, twf, logn, g, K);
   } else {
@@ -532,19 +603,19 @@ __device__ __forceinline__ void row_product(uint64_t (&va)[16], const uint64_t (
 }
 
 // Polymul row task with both operands in registers at once (2 CTAs per SM).
-template <bool HALVE, bool CG>
-__device__ __forceinline__ void row_task_polymul2(const uint64_t* ga, const uint64_t* gb,
-                                                  uint64_t* gc, bool single, uint64_t* smem,
-                                                  const TwPair* __restrict__ twf,
-                                                  const TwPair* __restrict__ twi,
-                                                  const LimbConst& K, uint32_t logn, uint32_t t,
-                                                  bool fused = false) {
+template <bool HALVE, bool CG, typename W>
+__device__ __forceinline__ void row_task_polymul2(const W* ga, const W* gb, W* gc, bool single,
+                                                  W* smem,
+                                                  const typename WordT<W>::Tw* __restrict__ twf,
+                                                  const typename WordT<W>::Tw* __restrict__ twi,
+                                                  const typename WordT<W>::LC& K, uint32_t logn,
+                                                  uint32_t t, bool fused = false) {
   const int th = threadIdx.x;
-  uint64_t* sa = smem;
-  uint64_t* sb = smem + kRowPad;
-  uint64_t va[16], vb[16];
+  W* sa = smem;
+  W* sb = smem + kRowPadW<W>;
+  W va[16], vb[16];
   rows_fwd2<CG>(va, vb, ga, gb, sa, sb, twf, logn, t, th, K.q, K.two_q, fused);
-  row_product(va, vb, fused, twf, logn, pass_geo(2, th, t).g, K);
+  row_product(va, vb, fused, twf, logn, pass_geo<W>(2, th, t).g, K);
   rows_inv<HALVE>(va, gc, single, sa, twi, logn, t, th, K, fused);
 }
 
@@ -554,25 +625,25 @@ __device__ __forceinline__ void row_task_polymul2(const uint64_t* ga, const uint
 // `gc` the output row.  `smem` holds 2 padded rows.
 // With `fused` the task follows Algorithm 8 (truncated transforms around
 // the pair step); K must then hold the fused constants (2/N).
-template <bool HALVE, bool CG>
-__device__ __forceinline__ void row_task_polymul(const uint64_t* ga, const uint64_t* gb,
-                                                 uint64_t* gc, bool single, uint64_t* smem,
-                                                 const TwPair* __restrict__ twf,
-                                                 const TwPair* __restrict__ twi,
-                                                 const LimbConst& K, uint32_t logn, uint32_t t,
-                                                 bool fused = false) {
+template <bool HALVE, bool CG, typename W>
+__device__ __forceinline__ void row_task_polymul(const W* ga, const W* gb, W* gc, bool single,
+                                                 W* smem,
+                                                 const typename WordT<W>::Tw* __restrict__ twf,
+                                                 const typename WordT<W>::Tw* __restrict__ twi,
+                                                 const typename WordT<W>::LC& K, uint32_t logn,
+                                                 uint32_t t, bool fused = false) {
   const int th = threadIdx.x;
-  uint64_t* sa = smem;
-  uint64_t* sb = smem + kRowPad;
-  uint64_t v[16];
+  W* sa = smem;
+  W* sb = smem + kRowPadW<W>;
+  W v[16];
   // operand a: keep its transform in smem (layout 2) while b is done
   rows_fwd<CG>(v, ga, sa, twf, logn, t, th, K.q, K.two_q, fused);
-  const PassGeo G2 = pass_geo(2, th, t);
+  const PassGeo G2 = pass_geo<W>(2, th, t);
   st_smem16(sa, G2, v);
   rows_fwd<CG>(v, gb, sb, twf, logn, t, th, K.q, K.two_q, fused);
   // product step in bit-reversed order (Algorithm 4 products, or Algorithm
   // 8's pair step); each thread re-reads only the words it stored itself
-  const uint64_t* a2 = sa + G2.pbase;
+  const W* a2 = sa + G2.pbase;
   if (fused)
     fused_pairs16_smem(v, a2, twf, logn, G2.g, K);
   else

@@ -26,4 +26,27 @@ struct alignas(16) TwPair {
   uint64_t wp;
 };
 
+// 32-bit words (moduli q < 2^30, Algorithm 4 with beta = 32): the same
+// constants in 32-bit fields.  mu = floor(2^(2m+1) / q) < 2^(m+2) <= 2^32.
+struct alignas(64) LimbConst32 {
+  uint32_t q;
+  uint32_t two_q;
+  uint32_t half_q1;
+  uint32_t mu;
+  uint32_t m;
+  uint32_t sh1;
+  uint32_t sh2;
+  uint32_t halving;
+  uint32_t ninv;
+  uint32_t ninv_p;
+  uint32_t w1ninv;
+  uint32_t w1ninv_p;
+};
+
+// 32-bit twiddle with its Shoup companion floor(w * 2^32 / q), 8 bytes.
+struct alignas(8) TwPair32 {
+  uint32_t w;
+  uint32_t wp;
+};
+
 }  // namespace pm
