@@ -16,15 +16,17 @@
 // (unlike a classical four-step FFT), because the merged transforms keep the
 // psi-powers inside the butterflies.
 //
-// Kernels
+// Kernels (each a template over the word type W, 64-bit or 32-bit)
 //   k_col_fwd<R>    : the n-12 forward column stages, streaming (registers
 //                     only, coalesced loads/stores), one thread per column.
-//   k_rows<MODE>    : the 12 in-row stages as three radix-16 passes; each
-//                     thread keeps 16 words per operand in registers and
-//                     rows are exchanged through padded shared memory between
-//                     passes.  For polymul the last forward pass, the
-//                     Barrett product (Algorithm 4) and the first inverse pass
-//                     run back to back in registers.
+//   k_rows2         : polymul rows: the 12 in-row stages of a and b together
+//                     (each thread holds 16 words of each operand), the
+//                     product step (Algorithm 4, or Algorithm 8's pair step)
+//                     and the 12 inverse in-row stages; rows are exchanged
+//                     through padded shared memory between the radix-16
+//                     passes.  The default polymul row kernel.
+//   k_rows<MODE>    : the same passes one operand at a time (forward or
+//                     inverse NTT rows, and polymul with row_ops 1).
 //   k_col_inv<R>    : the n-12 inverse column stages and the final reduction.
 //   k_fused13       : N = 2^13 in one CTA (column stage through smem).
 //   k_small         : N <= 2^11, one CTA per unit, radix-2 stages in smem.
