@@ -341,15 +341,21 @@ def run_gpu(args):
 
 
 def kernel_sources_sha1() -> str:
-    """Hash of the CUDA sources the kernels are built from."""
+    """Hash of the CUDA sources the kernels are built from, with comments and
+    whitespace removed (so that a comment edit keeps a captured figure)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2209_01290_gb300",
                         "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+            with open(os.path.join(csrc, f)) as fh:
+                code = fh.read()
+            code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+            code = re.sub(r"//[^\n]*", "", code)
+            code = re.sub(r"\s+", "", code)
+            h.update(f.encode() + b"\0" + code.encode())
     return h.hexdigest()
 
 

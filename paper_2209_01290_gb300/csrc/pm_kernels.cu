@@ -171,8 +171,13 @@ __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P
 // Each thread walks S columns (stride = the grid's thread count) and loads
 // column k+1 while it transforms column k, so that its loads are in flight
 // during the arithmetic.
+// 64-bit words with R = 32 keep 64 data registers per column: capping the
+// registers at 2 CTAs per SM (a few bytes of spill) beats 1 CTA per SM.
+template <int R, typename W>
+constexpr int kColMinBlocks = (R == 32 && sizeof(W) == 8) ? 2 : 1;
+
 template <int R, int S, typename W>
-__global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+__global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_fwd(KParams P, int nops) {
   const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * nops * kRow;
@@ -223,7 +228,7 @@ __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
 // reduction to [0, q); in place on c.  S columns per thread, software
 // pipelined as in k_col_fwd.
 template <int R, int S, bool HALVE, typename W>
-__global__ void __launch_bounds__(256) k_col_inv(KParams P) {
+__global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_inv(KParams P) {
   const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * kRow;
@@ -468,33 +473,37 @@ constexpr size_t kPipeMinCols = (size_t)1 << 20;
 template <int R, typename W>
 static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
   const size_t cols = (size_t)P.nunits * nops * kRow;
-  if (R < 32 && cols >= kPipeMinCols) {
-    constexpr int S = kColsPerThread;
-    const unsigned blocks = (unsigned)(((cols + S - 1) / S + 255) / 256);
-    k_col_fwd<R, S, W><<<blocks, 256, 0, st>>>(P, nops);
-  } else {
-    k_col_fwd<R, 1, W><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
+  if constexpr (R < 32) {  // R = 32 holds too many registers to pipeline columns
+    if (cols >= kPipeMinCols) {
+      constexpr int S = kColsPerThread;
+      const unsigned blocks = (unsigned)(((cols + S - 1) / S + 255) / 256);
+      k_col_fwd<R, S, W><<<blocks, 256, 0, st>>>(P, nops);
+      return cudaGetLastError();
+    }
   }
+  k_col_fwd<R, 1, W><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
   return cudaGetLastError();
 }
 
 template <int R, typename W>
 static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
   const size_t cols = (size_t)P.nunits * kRow;
-  const bool pipe = R < 32 && cols >= kPipeMinCols;
-  constexpr int S = kColsPerThread;
-  const unsigned blocks = (unsigned)((((pipe ? (cols + S - 1) / S : cols)) + 255) / 256);
-  if (pipe) {
-    if (P.halving)
-      k_col_inv<R, S, true, W><<<blocks, 256, 0, st>>>(P);
-    else
-      k_col_inv<R, S, false, W><<<blocks, 256, 0, st>>>(P);
-  } else {
-    if (P.halving)
-      k_col_inv<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
-    else
-      k_col_inv<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
+  if constexpr (R < 32) {  // as in launch_col_fwd
+    if (cols >= kPipeMinCols) {
+      constexpr int S = kColsPerThread;
+      const unsigned blocks = (unsigned)(((cols + S - 1) / S + 255) / 256);
+      if (P.halving)
+        k_col_inv<R, S, true, W><<<blocks, 256, 0, st>>>(P);
+      else
+        k_col_inv<R, S, false, W><<<blocks, 256, 0, st>>>(P);
+      return cudaGetLastError();
+    }
   }
+  const unsigned blocks = (unsigned)((cols + 255) / 256);
+  if (P.halving)
+    k_col_inv<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
+  else
+    k_col_inv<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 
