@@ -129,6 +129,31 @@ def _dist():
     return rank, ws, local, dist
 
 
+def replica_seed(rank: int) -> int:
+    """Input seed of one replica: every rank multiplies its own operands."""
+    from paper_2209_01290_gb300 import inputs
+    return inputs.seed_for(1) + 1000 * rank
+
+
+def replica_max(x: float, dist) -> float:
+    """Max over ranks of a per-rank float (the slowest replica decides the
+    job's time); the identity without a process group.  NCCL groups reduce on
+    the current CUDA device, others (gloo) on the host."""
+    if dist is None:
+        return x
+    import torch
+    dev = f"cuda:{torch.cuda.current_device()}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: int, steps: int, max_ms: float, world: int) -> float:
+    """Whole-job throughput under weak scaling: all ranks' products over the
+    slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
+
+
 def cpu_baseline(log2n: int, qs, psis, seconds: float = 12.0):
     """The oracle's scalar-NTT product on the host cores, on a bounded sample
     of the workload: as many products as fit in about `seconds`."""
@@ -208,7 +233,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     plan.reserve(npoly, stream=stream)
 
-    a, b = inputs.operand_pair(inputs.seed_for(1) + 1000 * rank, qs, npoly, n)
+    a, b = inputs.operand_pair(replica_seed(rank), qs, npoly, n)
     ha = torch.from_numpy(a.view(np.int64)).pin_memory()
     hb = torch.from_numpy(b.view(np.int64)).pin_memory()
     hc = torch.empty_like(ha).pin_memory()
@@ -256,17 +281,14 @@ def run_gpu(args):
     clocks = sampler.stop()
     capi.pm_plan_set_phase_events(plan.handle, [])
     torch.cuda.synchronize(dev)
-    elapsed_ms = start.elapsed_time(end)
+    elapsed_ms = replica_max(start.elapsed_time(end), dist)
     if dist is not None:
-        t = torch.tensor([elapsed_ms], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         dist.barrier()
     phase_ms = [[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(nphase - 1)]
                 for k in range(args.steps)]
     avg_phase = [sum(p[i] for p in phase_ms) / args.steps for i in range(nphase - 1)]
 
-    value = ws * units * args.steps / (elapsed_ms * 1e-3)
+    value = replica_value(units, args.steps, elapsed_ms, ws)
 
     # ---- end to end through the C ABI with host buffers
     e2e_steps = max(2, min(5, args.steps))
@@ -275,12 +297,8 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         plan.polymul_host(ha, hb, hc, da, db, dc, stream=stream)
-    e2e_dt = time.perf_counter() - t0
-    e2e_value = units / (e2e_dt / e2e_steps)
-    if dist is not None:
-        t = torch.tensor([e2e_dt], device=f"cuda:{dev}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_value = ws * units / (float(t.item()) / e2e_steps)
+    e2e_dt = replica_max(time.perf_counter() - t0, dist)
+    e2e_value = replica_value(units, e2e_steps, e2e_dt * 1e3, ws)
 
     # ---- roofline: the dominant kernel (rows, or the single fused kernel)
     if persistent:
