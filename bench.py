@@ -401,6 +401,11 @@ def _flush_l2(buf):
     buf.add_(1)  # writes 256 MiB: larger than the 129 MB L2
 
 
+def _sizes(args):
+    """log2 N values of the sweep workloads (fused, word32)."""
+    return [int(x) for x in args.sizes.split(",")]
+
+
 def _time_each(fn, reps, stream, flush=None):
     """Device time of fn() on `stream`, one event pair per call.  The L2
     flush runs on the same stream, before the start event, so that it is
@@ -577,11 +582,11 @@ def run_workload(args):
     elif args.workload == "fused":
         # Eq. 2 vs Algorithm 8 products, batched (~1 GiB of operands per
         # step) for N = 2^12 .. 2^17; the two plans alternate step by step
-        for log2n in range(12, 18):
+        for log2n in _sizes(args):
             n = 1 << log2n
             qs, psis = capi.pm_find_params(log2n, 1, 60)
             plans = {"eq2": Plan(n, qs, psis), "alg8": Plan(n, qs, psis, fused=True)}
-            P = max(1, (1 << 26) // n)
+            P = args.products or max(1, (1 << 26) // n)
             A = inputs.uniform_limbs_torch(log2n, qs, P, n, device=dev)
             B = inputs.uniform_limbs_torch(log2n + 100, qs, P, n, device=dev)
             C = torch.empty_like(A)
@@ -604,10 +609,10 @@ def run_workload(args):
     elif args.workload == "word32":
         # 30-bit primes: 32-bit words (PM_PLAN_WORD32) vs the same primes in
         # 64-bit words; batched products (~1 GiB of 64-bit operands per step)
-        for log2n in range(12, 18):
+        for log2n in _sizes(args):
             n = 1 << log2n
             qs, psis = capi.pm_find_params(log2n, 1, 30)
-            P = max(1, (1 << 26) // n)
+            P = args.products or max(1, (1 << 26) // n)
             A = inputs.uniform_limbs_torch(log2n, qs, P, n, device=dev)
             B = inputs.uniform_limbs_torch(log2n + 100, qs, P, n, device=dev)
             A32, B32 = A.to(torch.int32), B.to(torch.int32)
@@ -719,6 +724,10 @@ def main():
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom",
                              "fused", "word32"])
+    ap.add_argument("--sizes", default="12,13,14,15,16,17",
+                    help="log2 N values for --workload fused / word32")
+    ap.add_argument("--products", type=int, default=0,
+                    help="products per step for --workload fused / word32 (0: ~1 GiB)")
     ap.add_argument("--fused", action="store_true",
                     help="headline products by Algorithm 8 (PM_PLAN_FUSED)")
     ap.add_argument("--tom-count", type=int, default=1 << 15)

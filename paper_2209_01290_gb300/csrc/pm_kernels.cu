@@ -171,13 +171,14 @@ __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P
 // Each thread walks S columns (stride = the grid's thread count) and loads
 // column k+1 while it transforms column k, so that its loads are in flight
 // during the arithmetic.
-// 64-bit words with R = 32 keep 64 data registers per column: capping the
-// registers at 2 CTAs per SM (a few bytes of spill) beats 1 CTA per SM.
-template <int R, typename W>
-constexpr int kColMinBlocks = (R == 32 && sizeof(W) == 8) ? 2 : 1;
-
+// The column kernels are __device__ bodies with two __global__ wrappers:
+// k_col_* with the compiler's own register choice, and k_col_*_cap compiled
+// for 2 CTAs per SM.  The capped form serves 64-bit words with R = 32, whose
+// 64 data registers per column otherwise leave 1 CTA per SM (the cap costs a
+// few bytes of spill and gains ~8% at N = 2^17).  An explicit minimum of 1
+// is not the same as none: the compiler then takes more registers.
 template <int R, int S, typename W>
-__global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_fwd(KParams P, int nops) {
+__device__ __forceinline__ void col_fwd_body(const KParams& P, int nops) {
   const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * nops * kRow;
@@ -224,11 +225,21 @@ __global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_fwd(KParams P,
   }
 }
 
+template <int R, int S, typename W>
+__global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
+  col_fwd_body<R, S, W>(P, nops);
+}
+
+template <int R, int S, typename W>
+__global__ void __launch_bounds__(256, 2) k_col_fwd_cap(KParams P, int nops) {
+  col_fwd_body<R, S, W>(P, nops);
+}
+
 // Inverse column stages (the last log2 R stages of Algorithm 7) plus the
 // reduction to [0, q); in place on c.  S columns per thread, software
 // pipelined as in k_col_fwd.
 template <int R, int S, bool HALVE, typename W>
-__global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_inv(KParams P) {
+__device__ __forceinline__ void col_inv_body(const KParams& P) {
   const KView<W> V(P);
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * kRow;
@@ -268,6 +279,16 @@ __global__ void __launch_bounds__(256, kColMinBlocks<R, W>) k_col_inv(KParams P)
     if (!more) break;
     gid = nid;
   }
+}
+
+template <int R, int S, bool HALVE, typename W>
+__global__ void __launch_bounds__(256) k_col_inv(KParams P) {
+  col_inv_body<R, S, HALVE, W>(P);
+}
+
+template <int R, int S, bool HALVE, typename W>
+__global__ void __launch_bounds__(256, 2) k_col_inv_cap(KParams P) {
+  col_inv_body<R, S, HALVE, W>(P);
 }
 
 // N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
@@ -481,7 +502,11 @@ static cudaError_t launch_col_fwd(const KParams& P, int nops, cudaStream_t st) {
       return cudaGetLastError();
     }
   }
-  k_col_fwd<R, 1, W><<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(P, nops);
+  const unsigned blocks = (unsigned)((cols + 255) / 256);
+  if constexpr (R == 32 && sizeof(W) == 8)
+    k_col_fwd_cap<R, 1, W><<<blocks, 256, 0, st>>>(P, nops);
+  else
+    k_col_fwd<R, 1, W><<<blocks, 256, 0, st>>>(P, nops);
   return cudaGetLastError();
 }
 
@@ -500,10 +525,17 @@ static cudaError_t launch_col_inv(const KParams& P, cudaStream_t st) {
     }
   }
   const unsigned blocks = (unsigned)((cols + 255) / 256);
-  if (P.halving)
-    k_col_inv<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
-  else
-    k_col_inv<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
+  if constexpr (R == 32 && sizeof(W) == 8) {
+    if (P.halving)
+      k_col_inv_cap<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
+    else
+      k_col_inv_cap<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
+  } else {
+    if (P.halving)
+      k_col_inv<R, 1, true, W><<<blocks, 256, 0, st>>>(P);
+    else
+      k_col_inv<R, 1, false, W><<<blocks, 256, 0, st>>>(P);
+  }
   return cudaGetLastError();
 }
 
