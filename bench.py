@@ -455,7 +455,7 @@ def run_workload(args):
                       "p50_us": 1e3 * float(np.median(lat)), "p99_us": 1e3 * float(np.percentile(lat, 99)),
                       "back_to_back_polymuls_per_s": 1000 / (e0.elapsed_time(e1) * 1e-3)})
     elif args.workload == "c2sweep":
-        for log2n in range(13, 18):
+        for log2n in [x for x in _sizes(args) if x >= 13]:
             n = 1 << log2n
             qs, psis = capi.pm_find_params(log2n, 1, 60)
             plan = Plan(n, qs, psis)
@@ -725,7 +725,7 @@ def main():
                     choices=["headline", "c1", "c2sweep", "c3", "c4", "c5", "reductions", "tom",
                              "fused", "word32"])
     ap.add_argument("--sizes", default="12,13,14,15,16,17",
-                    help="log2 N values for --workload fused / word32")
+                    help="log2 N values for --workload fused / word32 / c2sweep (>= 13)")
     ap.add_argument("--products", type=int, default=0,
                     help="products per step for --workload fused / word32 (0: ~1 GiB)")
     ap.add_argument("--fused", action="store_true",
