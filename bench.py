@@ -306,9 +306,14 @@ def run_gpu(args):
         dom_mulmods = mulmods_per_polymul(log2n) * units
     elif log2n >= 14:
         dom_idx = 1
-        dom_name = ("k_rows2<POLYMUL> (in-row stages of a and b together, Barrett pointwise, "
-                    "inverse in-row stages)" if tuning.row_ops == 2 else
-                    "k_rows<POLYMUL> (in-row stages + Barrett pointwise)")
+        row_ops = tuning.row_ops
+        if row_ops == 0:  # the library's choice by batch size
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            row_ops = 3 if (units << (log2n - 12)) <= sms else 2
+        dom_name = {2: "k_rows2<POLYMUL> (in-row stages of a and b together, Barrett pointwise, "
+                       "inverse in-row stages)",
+                    3: "k_rows_lat<POLYMUL> (1024 threads per row, radix-4 passes)",
+                    1: "k_rows<POLYMUL> (in-row stages + Barrett pointwise)"}[row_ops]
         dom_mulmods = rows_kernel_mulmods(log2n) * units
     else:
         dom_idx, dom_name = 0, "fused single-kernel polymul"

@@ -315,10 +315,16 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  *                           the pipeline distances in units, ctas_per_sm the
  *                           resident CTAs per SM).  Uses a control block of
  *                           16 + 8 * units bytes in the stream's scratch.
- * row_ops (SPLIT only): 1 = the row kernel transforms a then b (3 CTAs per
- * SM), 2 = both together sharing twiddle loads (2 CTAs per SM).
+ * row_ops (SPLIT only; the in-row stages of N >= 4096):
+ *   1 = 256 threads per row, a transformed before b (3 CTAs per SM);
+ *   2 = 256 threads per row, a and b together sharing twiddle loads
+ *       (2 CTAs per SM) -- the throughput kernel;
+ *   3 = 1024 threads per row in radix-4 passes (1 CTA per SM) -- for
+ *       batches too small to fill the GPU (also used by pm_ntt_fwd/inv);
+ *   0 = by batch size: 3 while the batch has at most (SM count) rows of
+ *       4096 words, else 2 (pm_ntt_fwd/inv: 3, else 1).
  * pm_plan_autotune() picks these by timing; without it a plan uses SPLIT,
- * row_ops 2 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
+ * row_ops 0 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
 enum { PM_VARIANT_SPLIT = 0, PM_VARIANT_PERSISTENT = 1 };
 typedef struct pm_tuning {
     int32_t variant;

@@ -250,7 +250,7 @@ class PmTuning(ctypes.Structure):
 
 
 def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 3, lag_fwd: int = 8,
-                 lag_inv: int = 64, row_ops: int = 2) -> None:
+                 lag_inv: int = 64, row_ops: int = 0) -> None:
     t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv, row_ops)
     _call("pm_plan_tune", plan, ctypes.byref(t))
 

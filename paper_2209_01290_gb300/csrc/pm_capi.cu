@@ -143,7 +143,12 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.nlimbs = p->nlimbs;
   P.nunits = npoly * p->nlimbs;
   P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
-  P.row_ops = p->tune.row_ops == 2 ? 2 : 1;
+  // row kernel: 1 = k_rows, 2 = k_rows2, 3 = k_rows_lat; 0 = by batch size:
+  // the 1024-thread latency rows while the batch has at most one row per SM
+  // (measured faster there), the two-operand throughput rows above
+  const uint64_t row_ctas = p->logn >= 12 ? (uint64_t)P.nunits << (p->logn - 12) : 0;
+  P.row_ops = p->tune.row_ops ? p->tune.row_ops
+                              : (row_ctas <= (uint64_t)p->num_sms ? 3u : 2u);
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
   P.word32 = is_word32(p) ? 1 : 0;
   return P;
@@ -357,7 +362,7 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   p->tune.ctas_per_sm = 3;
   p->tune.lag_fwd = 8;
   p->tune.lag_inv = 64;
-  p->tune.row_ops = 2;
+  p->tune.row_ops = 0;
   p->logn = log2n;
   p->nlimbs = nlimbs;
   p->q.assign(q, q + nlimbs);
@@ -824,7 +829,7 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
   if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
     return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
-  if (t->row_ops != 1 && t->row_ops != 2) return fail(PM_ERR_ARG, "row_ops must be 1 or 2");
+  if (t->row_ops > 3) return fail(PM_ERR_ARG, "row_ops must be 0..3");
   if (t->variant == PM_VARIANT_PERSISTENT && is_word32(plan))
     return fail(PM_ERR_ARG, "the persistent variant takes 64-bit plans");
   if (t->variant == PM_VARIANT_PERSISTENT &&
@@ -848,7 +853,10 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
   // with a few pipeline distances
   std::vector<pm_tuning> cand;
   cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
-  if (plan->logn >= 12 && plan->logn != 13) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
+  if (plan->logn >= 12 && plan->logn != 13) {
+    cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
+    cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 3});
+  }
   if (plan->logn >= 13 && !is_word32(plan)) {
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});

@@ -164,6 +164,56 @@ __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P
                                   V.c + off, single, smem, twf, twi, K, logn, t, FUSED);
 }
 
+// Rows for small batches: the same row task as k_rows2 (or k_rows for the
+// forward and inverse NTT) over 1024 threads per row in six radix-4 passes,
+// one CTA per SM; see the latency pipeline in pm_passes.cuh.
+template <int MODE, bool HALVE, typename W>
+__global__ void __launch_bounds__(kLatThreads, 1) k_rows_lat(KParams P) {
+  extern __shared__ __align__(16) uint64_t smem_raw[];
+  W* sa = reinterpret_cast<W*>(smem_raw);
+  W* sb = sa + kLatRowPad<W>;
+  const KView<W> V(P);
+  const uint32_t logn = P.logn;
+  const uint32_t unit = blockIdx.x >> (logn - kRowLog);
+  const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
+  if (unit >= P.nunits) return;
+  const uint32_t limb = unit % P.nlimbs;
+  const auto K = ld_limb(V.lc + limb);
+  const auto* twf = V.twf + ((size_t)limb << logn);
+  const auto* twi = V.twi + ((size_t)limb << logn);
+  const size_t off = ((size_t)unit << logn) + (size_t)t * kRow;
+  const bool single = (logn == kRowLog);
+  const int th = threadIdx.x;
+  W va[4], vb[4];
+  if constexpr (MODE == MODE_INV) {
+    // bit-reversed input in the last forward layout: words 4 th .. 4 th + 3
+#pragma unroll
+    for (int u = 0; u < 4; u++) va[u] = __ldcs(V.c + off + 4 * th + u);
+    lat_inv<HALVE>(va, V.c + off, single, sa, twi, logn, t, th, K, false);
+  } else if constexpr (MODE == MODE_FWD) {
+    lat_fwd<false>(va, vb, V.c + off, (const W*)nullptr, sa, sb, twf, logn, t, th, K.q, K.two_q,
+                   false);
+#pragma unroll
+    for (int u = 0; u < 4; u++) __stcs(V.c + off + 4 * th + u, reduce4(va[u], K.q, K.two_q));
+  } else {
+    constexpr bool kFused = (MODE == MODE_POLYMUL_FUSED);
+    lat_fwd<true>(va, vb, (single ? V.a : V.c) + off, (single ? V.b : V.s) + off, sa, sb, twf,
+                  logn, t, th, K.q, K.two_q, kFused);
+    if constexpr (kFused) {
+      // Algorithm 8's pair step: positions 4 th + u of row t are pairs
+      // i = 2 (1024 t + th) (even) and i + 1 (odd), floor(i/2) = 1024 t + th
+      const auto w = ld_tw(twf + (1u << (logn - 2)) + (t << 10) + th);
+      fused_pair<false>(va[0], va[1], vb[0], vb[1], w, K);
+      fused_pair<true>(va[2], va[3], vb[2], vb[3], w, K);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+        va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
+    }
+    lat_inv<HALVE>(va, V.c + off, single, sa, twi, logn, t, th, K, kFused);
+  }
+}
+
 // Forward column stages for n = 12 + log2 R, R in {2..32}: thread = (unit,
 // operand, column); loads the R words {c + 4096 t}, runs the first log2 R
 // stages of Algorithm 6, stores them back in place (to `dst`).
@@ -568,10 +618,20 @@ constexpr int kRowsSmem = 2 * kRowPadW<W> * (int)sizeof(W);
 template <typename W>
 constexpr int kFused13Smem = 4 * kRowPadW<W> * (int)sizeof(W);
 
+template <typename W>
+constexpr int kLatSmem = 2 * kLatRowPad<W> * (int)sizeof(W);
+
 template <int MODE, typename W>
 static cudaError_t rows(const KParams& P, cudaStream_t st) {
   const unsigned blocks = P.nunits << (P.logn - kRowLog);
   constexpr int smem = kRowsSmem<W>;
+  if (P.row_ops == 3) {
+    if (P.halving)
+      k_rows_lat<MODE, true, W><<<blocks, kLatThreads, kLatSmem<W>, st>>>(P);
+    else
+      k_rows_lat<MODE, false, W><<<blocks, kLatThreads, kLatSmem<W>, st>>>(P);
+    return cudaGetLastError();
+  }
   if ((MODE == MODE_POLYMUL || MODE == MODE_POLYMUL_FUSED) && P.row_ops == 2) {
     constexpr bool F = (MODE == MODE_POLYMUL_FUSED);
     if (P.halving)
@@ -615,6 +675,10 @@ static cudaError_t prepare_mode() {
                             (const void*)k_rows2<H, true, W>,
                             (const void*)k_rows<MODE_FWD, H, W>,
                             (const void*)k_rows<MODE_INV, H, W>};
+  const void* lat_fns[] = {(const void*)k_rows_lat<MODE_POLYMUL, H, W>,
+                           (const void*)k_rows_lat<MODE_POLYMUL_FUSED, H, W>,
+                           (const void*)k_rows_lat<MODE_FWD, H, W>,
+                           (const void*)k_rows_lat<MODE_INV, H, W>};
   const void* f13_fns[] = {(const void*)k_fused13<MODE_POLYMUL, H, W>,
                            (const void*)k_fused13<MODE_POLYMUL_FUSED, H, W>,
                            (const void*)k_fused13<MODE_FWD, H, W>,
@@ -624,6 +688,8 @@ static cudaError_t prepare_mode() {
     if ((e = set_smem(f, rs)) != cudaSuccess) return e;
   for (const void* f : f13_fns)
     if ((e = set_smem(f, fs)) != cudaSuccess) return e;
+  for (const void* f : lat_fns)
+    if ((e = set_smem(f, kLatSmem<W>)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 

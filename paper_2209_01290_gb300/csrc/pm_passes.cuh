@@ -651,4 +651,222 @@ __device__ __forceinline__ void row_task_polymul(const W* ga, const W* gb, W* gc
   rows_inv<HALVE>(v, gc, single, sa, twi, logn, t, th, K, fused);
 }
 
+// ------------------------------------------------- latency row pipeline
+// The 12 in-row stages of a 4096-word row as six radix-4 passes over 1024
+// threads (4 words per thread and operand): a row task spread over 32 warps
+// of one SM, for batches too small to fill the GPU with the radix-16 rows.
+// Pass p (forward order) covers in-row stages 2p, 2p+1; its groups are 4
+// words spaced 2^e apart, e = 10 - 2p, inside blocks of 2^(e+2) words:
+//   j = blk 2^(e+2) + off + u 2^e,  off < 2^e.
+// Threads are mapped offset-fastest for e >= 4 (a half-warp or warp reads
+// consecutive words) and block-fastest for e < 4.  Shared memory is padded
+// one word per 16 (64-bit words) or per 32 (32-bit words): all six layouts
+// are then free of bank conflicts for 64-bit words, and have one 2-way
+// conflict (pass e = 4) for 32-bit words.  The inverse runs the layouts in
+// reverse order (GS stages 2p', 2p'+1 on the layout of pass 5 - p').
+constexpr int kLatThreads = 1024;
+
+template <typename W>
+constexpr int kLatShift = sizeof(W) == 8 ? 4 : 5;
+template <typename W>
+constexpr int kLatRowPad = kRow + (kRow >> kLatShift<W>);
+
+struct LatGeo {
+  int pbase;    // padded smem index of u = 0
+  uint32_t g;   // block index of the group within the whole transform
+};
+
+template <typename W>
+__device__ __forceinline__ LatGeo lat_geo(int p, int th, uint32_t t) {
+  const int e = 10 - 2 * p;
+  int blk, off;
+  if (e >= 4) {
+    off = th & ((1 << e) - 1);
+    blk = th >> e;
+  } else {
+    blk = th & ((1 << (10 - e)) - 1);
+    off = th >> (10 - e);
+  }
+  const int j0 = (blk << (e + 2)) + off;
+  LatGeo G;
+  G.pbase = j0 + (j0 >> kLatShift<W>);
+  G.g = (t << (2 * p)) + (uint32_t)blk;
+  return G;
+}
+
+// Padded offset of word u of a group relative to u = 0 (compile-time per
+// pass): u 2^e plus the pad words crossed (none inside the group's 16- or
+// 32-word block when the stride is small; for 32-bit words and e = 4 the
+// group starts at offset off < 16 of its 32-word block).
+template <typename W, int E>
+__device__ __forceinline__ constexpr int lat_off(int u) {
+  constexpr int S = kLatShift<W>;
+  if constexpr (E >= S)
+    return u * ((1 << E) + (1 << (E - S)));
+  else if constexpr (E == 4)
+    return 16 * u + (u >> 1);
+  else
+    return u << E;
+}
+
+template <typename W, int E>
+__device__ __forceinline__ void lat_ld(W (&v)[4], const W* s, int pbase) {
+#pragma unroll
+  for (int u = 0; u < 4; u++) v[u] = s[pbase + lat_off<W, E>(u)];
+}
+
+template <typename W, int E>
+__device__ __forceinline__ void lat_st(W* s, int pbase, const W (&v)[4]) {
+#pragma unroll
+  for (int u = 0; u < 4; u++) s[pbase + lat_off<W, E>(u)] = v[u];
+}
+
+// Two consecutive merged-CT stages on a group of 4 words (global stages s0,
+// s0+1; the group is block g at stage s0): stage s0 pairs (u, u+2) with
+// twiddle Psi_br[2^s0 + g]; stage s0+1 pairs (u, u+1) with
+// Psi_br[2^(s0+1) + 2g + u/2].  skip_last omits the second stage.
+template <typename W>
+__device__ __forceinline__ void ct4(W (&v)[4], const typename WordT<W>::Tw* __restrict__ tw,
+                                    uint32_t s0, uint32_t g, W q, W two_q, bool skip_last) {
+  const auto t0 = ld_tw(tw + (1u << s0) + g);
+  ct_bfly(v[0], v[2], t0.w, t0.wp, q, two_q);
+  ct_bfly(v[1], v[3], t0.w, t0.wp, q, two_q);
+  if (!skip_last) {
+    typename WordT<W>::Tw t1[2];
+    ld_tw2(tw + (1u << (s0 + 1)) + 2 * g, t1[0], t1[1]);
+    ct_bfly(v[0], v[1], t1[0].w, t1[0].wp, q, two_q);
+    ct_bfly(v[2], v[3], t1[1].w, t1[1].wp, q, two_q);
+  }
+}
+
+// The same on two operands sharing the twiddles.
+template <typename W>
+__device__ __forceinline__ void ct4_2(W (&va)[4], W (&vb)[4],
+                                      const typename WordT<W>::Tw* __restrict__ tw, uint32_t s0,
+                                      uint32_t g, W q, W two_q, bool skip_last) {
+  const auto t0 = ld_tw(tw + (1u << s0) + g);
+  ct_bfly(va[0], va[2], t0.w, t0.wp, q, two_q);
+  ct_bfly(va[1], va[3], t0.w, t0.wp, q, two_q);
+  ct_bfly(vb[0], vb[2], t0.w, t0.wp, q, two_q);
+  ct_bfly(vb[1], vb[3], t0.w, t0.wp, q, two_q);
+  if (!skip_last) {
+    typename WordT<W>::Tw t1[2];
+    ld_tw2(tw + (1u << (s0 + 1)) + 2 * g, t1[0], t1[1]);
+    ct_bfly(va[0], va[1], t1[0].w, t1[0].wp, q, two_q);
+    ct_bfly(va[2], va[3], t1[1].w, t1[1].wp, q, two_q);
+    ct_bfly(vb[0], vb[1], t1[0].w, t1[0].wp, q, two_q);
+    ct_bfly(vb[2], vb[3], t1[1].w, t1[1].wp, q, two_q);
+  }
+}
+
+// Two consecutive merged-GS stages on a group of 4 words (GS stages sig0,
+// sig0+1; the group is block g of 2^(sig0+2) words): stage sig0 pairs
+// (u, u+1) with twiddle Psi^-1_br[(N >> (sig0+1)) + 2g + u/2]; stage sig0+1
+// pairs (u, u+2) with Psi^-1_br[(N >> (sig0+2)) + g].  skip_first omits the
+// first stage.
+template <bool HALVE, typename W>
+__device__ __forceinline__ void gs4(W (&v)[4], const typename WordT<W>::Tw* __restrict__ tw,
+                                    uint32_t logn, uint32_t sig0, uint32_t g, W q, W two_q, W hq,
+                                    bool skip_first) {
+  if (!skip_first) {
+    typename WordT<W>::Tw t0[2];
+    ld_tw2(tw + (1u << (logn - sig0 - 1)) + 2 * g, t0[0], t0[1]);  // even index
+    gs_bfly_mode<HALVE>(v[0], v[1], t0[0].w, t0[0].wp, q, two_q, hq);
+    gs_bfly_mode<HALVE>(v[2], v[3], t0[1].w, t0[1].wp, q, two_q, hq);
+  }
+  const auto t1 = ld_tw(tw + (1u << (logn - sig0 - 2)) + g);
+  gs_bfly_mode<HALVE>(v[0], v[2], t1.w, t1.wp, q, two_q, hq);
+  gs_bfly_mode<HALVE>(v[1], v[3], t1.w, t1.wp, q, two_q, hq);
+}
+
+// One forward pass of the latency pipeline (compile-time pass index P).
+// Pass 0 reads the global row when g_src (layout e = 10 is th + 1024 u);
+// other passes read their layout from smem.  With two operands (vb != null)
+// both are transformed with shared twiddles.
+template <int P, bool TWO, typename W>
+__device__ __forceinline__ void lat_fwd_pass(W (&va)[4], W (&vb)[4], const W* ga, const W* gb,
+                                             W* sa, W* sb,
+                                             const typename WordT<W>::Tw* __restrict__ twf,
+                                             uint32_t logn, uint32_t t, int th, W q, W two_q,
+                                             bool trunc) {
+  constexpr int E = 10 - 2 * P;
+  const LatGeo G = lat_geo<W>(P, th, t);
+  if (P == 0 && ga) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      va[u] = ld_g<false>(ga + th + 1024 * u);
+      if constexpr (TWO) vb[u] = ld_g<false>(gb + th + 1024 * u);
+    }
+  } else {
+    lat_ld<W, E>(va, sa, G.pbase);
+    if constexpr (TWO) lat_ld<W, E>(vb, sb, G.pbase);
+  }
+  const uint32_t s0 = logn - 12 + 2 * P;
+  if constexpr (TWO)
+    ct4_2(va, vb, twf, s0, G.g, q, two_q, trunc && P == 5);
+  else
+    ct4(va, twf, s0, G.g, q, two_q, trunc && P == 5);
+  if constexpr (P < 5) {
+    lat_st<W, E>(sa, G.pbase, va);
+    if constexpr (TWO) lat_st<W, E>(sb, G.pbase, vb);
+    __syncthreads();
+  }
+}
+
+// Forward in-row stages (six passes); leaves the words of the last layout
+// (e = 0: thread th holds words 4 th .. 4 th + 3) in va (and vb).
+template <bool TWO, typename W>
+__device__ __forceinline__ void lat_fwd(W (&va)[4], W (&vb)[4], const W* ga, const W* gb, W* sa,
+                                        W* sb, const typename WordT<W>::Tw* __restrict__ twf,
+                                        uint32_t logn, uint32_t t, int th, W q, W two_q,
+                                        bool trunc) {
+  lat_fwd_pass<0, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+  lat_fwd_pass<1, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+  lat_fwd_pass<2, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+  lat_fwd_pass<3, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+  lat_fwd_pass<4, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+  lat_fwd_pass<5, TWO>(va, vb, ga, gb, sa, sb, twf, logn, t, th, q, two_q, trunc);
+}
+
+// One inverse pass (GS stages 2P', 2P'+1 on the layout of forward pass
+// 5 - P').  The first pass works on the registers it is given.
+template <int PI, bool HALVE, typename W>
+__device__ __forceinline__ void lat_inv_pass(W (&v)[4], W* s,
+                                             const typename WordT<W>::Tw* __restrict__ twi,
+                                             uint32_t logn, uint32_t t, int th, W q, W two_q,
+                                             W hq, bool trunc) {
+  constexpr int PF = 5 - PI;
+  constexpr int E = 10 - 2 * PF;
+  const LatGeo G = lat_geo<W>(PF, th, t);
+  if constexpr (PI > 0) lat_ld<W, E>(v, s, G.pbase);
+  gs4<HALVE>(v, twi, logn, 2 * PI, G.g, q, two_q, hq, trunc && PI == 0);
+  if constexpr (PI < 5) {
+    lat_st<W, E>(s, G.pbase, v);
+    __syncthreads();
+  }
+}
+
+// Inverse in-row stages; the result (layout e = 10: words th + 1024 u) goes
+// to the global row g_dst, canonical and times N^-1 when `final` (the row is
+// the whole transform and 1/N is not applied per stage), else lazy.
+template <bool HALVE, typename W>
+__device__ __forceinline__ void lat_inv(W (&v)[4], W* g_dst, bool final, W* s,
+                                        const typename WordT<W>::Tw* __restrict__ twi,
+                                        uint32_t logn, uint32_t t, int th,
+                                        const typename WordT<W>::LC& K, bool trunc) {
+  const W q = K.q, two_q = K.two_q, hq = K.half_q1;
+  lat_inv_pass<0, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  lat_inv_pass<1, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  lat_inv_pass<2, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  lat_inv_pass<3, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  lat_inv_pass<4, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  lat_inv_pass<5, HALVE>(v, s, twi, logn, t, th, q, two_q, hq, trunc);
+  if (!HALVE && final) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) v[u] = mul_shoup_lazy(v[u], K.ninv, K.ninv_p, q);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++) __stcs(g_dst + th + 1024 * u, final ? csub(v[u], q) : v[u]);
+}
+
 }  // namespace pm

@@ -38,7 +38,7 @@ def test_tuning_validation():
     from paper_2209_01290_gb300 import capi
     plan, *_ = _setup(14, 1, 1, 1)
     t = capi.pm_plan_get_tuning(plan.handle)
-    assert t.variant == capi.PM_VARIANT_SPLIT and t.ctas_per_sm == 3 and t.row_ops == 2
+    assert t.variant == capi.PM_VARIANT_SPLIT and t.ctas_per_sm == 3 and t.row_ops == 0
     for bad in [(capi.PM_VARIANT_PERSISTENT, 0, 8, 16), (capi.PM_VARIANT_PERSISTENT, 3, 8, 8),
                 (capi.PM_VARIANT_PERSISTENT, 4, 8, 16), (7, 3, 8, 16)]:
         with pytest.raises(capi.PMError) as e:
