@@ -253,6 +253,18 @@ pm_status pm_queue_reserve(pm_queue *q, uint64_t units, uint64_t scratch_words);
  * be serialised on one stream (they share its buffers). */
 pm_status pm_polymul_uneven(pm_queue *q, const pm_job *jobs, uint32_t njobs, void *stream);
 
+/* How pm_polymul_uneven runs the jobs with N >= 4096:
+ *   PM_UNEVEN_PERSISTENT: one persistent work-queue launch (above);
+ *   PM_UNEVEN_GROUPED: the units grouped by N, each group through the column
+ *     and row kernels of pm_polymul (up to three launches per distinct N,
+ *     every unit's pointers and tables from a descriptor table) -- no
+ *     dependency waits, the throughput kernels;
+ *   PM_UNEVEN_AUTO (default): GROUPED when the batch has at least 8 rows of
+ *     4096 words per SM, else PERSISTENT.
+ * Results are identical; PM_ERR_ARG for another value. */
+enum { PM_UNEVEN_AUTO = 0, PM_UNEVEN_PERSISTENT = 1, PM_UNEVEN_GROUPED = 2 };
+pm_status pm_queue_set_mode(pm_queue *q, int mode);
+
 /* Synchronise `stream` and report PM_ERR_TIMEOUT if an uneven launch on this
  * queue gave up waiting for a dependency. */
 pm_status pm_queue_sync(pm_queue *q, void *stream);

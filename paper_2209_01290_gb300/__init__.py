@@ -192,9 +192,12 @@ class Graph:
 class Queue:
     """Reusable context for uneven batches (pm_polymul_uneven)."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, mode: int = 0):
+        """mode: capi.PM_UNEVEN_AUTO (0), _PERSISTENT (1) or _GROUPED (2)."""
         self.device = device
         self._h = capi.pm_queue_create(device)
+        if mode:
+            capi.pm_queue_set_mode(self._h, mode)
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -72,6 +72,7 @@ SIGNATURES = {
     "pm_queue_reserve": (_i32, [_vp, _u64, _u64]),
     "pm_polymul_uneven": (_i32, [_vp, _vp, _u32, _vp]),
     "pm_queue_sync": (_i32, [_vp, _vp]),
+    "pm_queue_set_mode": (_i32, [_vp, _i32]),
 }
 
 _lib = None
@@ -308,6 +309,13 @@ def pm_graph_destroy(g: int) -> None:
 class PmJob(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("c", ctypes.c_void_p), ("npoly", ctypes.c_uint32)]
+
+
+PM_UNEVEN_AUTO, PM_UNEVEN_PERSISTENT, PM_UNEVEN_GROUPED = 0, 1, 2
+
+
+def pm_queue_set_mode(q: int, mode: int) -> None:
+    _call("pm_queue_set_mode", q, mode)
 
 
 def pm_queue_create(device: int = 0) -> int:

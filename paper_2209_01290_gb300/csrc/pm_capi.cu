@@ -931,6 +931,10 @@ pm_status pm_plan_get_tuning(const pm_plan* plan, pm_tuning* t) {
 
 // ---------------------------------------------------------------- uneven batch
 
+// Uneven batches with at least this many 4096-word rows per SM take the
+// grouped split launches under PM_UNEVEN_AUTO.
+constexpr uint64_t kGroupedMinRows = 8;
+
 struct pm_queue {
   int device = 0;
   int num_sms = 0;
@@ -946,6 +950,7 @@ struct pm_queue {
   size_t h_cap = 0;
   cudaEvent_t staged = nullptr;  // the last upload from the staging buffers
   bool staged_used = false;
+  int mode = 0;  // PM_UNEVEN_AUTO / _PERSISTENT / _GROUPED
 };
 
 namespace {
@@ -1051,6 +1056,15 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   if (units == 0) return ok();
   pm_status s = queue_reserve(q, units, scratch ? scratch : 1);
   if (s != PM_OK) return s;
+  // grouped split launches for large batches (each N's units through the
+  // column and row kernels of the uniform path), the persistent work queue
+  // for small ones (its overlap of the three phases matters there)
+  uint64_t rows_total = 0;
+  for (uint32_t j = 0; j < njobs; ++j)
+    if (jobs[j].plan->logn >= 12)
+      rows_total += ((uint64_t)jobs[j].npoly * jobs[j].plan->nlimbs) << (jobs[j].plan->logn - 12);
+  const bool grouped = q->mode == PM_UNEVEN_GROUPED ||
+                       (q->mode == PM_UNEVEN_AUTO && rows_total >= kGroupedMinRows * (uint64_t)q->num_sms);
   if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
     return cuda_fail(e, "queue staging");
   // unit descriptors and section prefix counts
@@ -1097,6 +1111,36 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       tw += (uint32_t)(n >> 12);
       ti += split ? 16u : 0u;
     }
+  }
+  if (grouped) {
+    // units sorted by N (stable), one grouped launch per N
+    std::vector<pm::UnitDesc> sorted(units);
+    uint32_t count[18] = {0}, start[18] = {0};
+    for (size_t i = 0; i < units; ++i) count[q->h_units[i].logn]++;
+    for (int L = 13; L < 18; ++L) start[L] = start[L - 1] + count[L - 1];
+    for (size_t i = 0; i < units; ++i) sorted[start[q->h_units[i].logn]++] = q->h_units[i];
+    std::copy(sorted.begin(), sorted.end(), q->h_units);
+    if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
+      return cuda_fail(e, "queue upload");
+    q->staged_used = true;
+    size_t first = 0;
+    for (int L = 12; L < 18; ++L) {
+      if (!count[L]) continue;
+      pm::KParams P{};
+      P.desc = q->d_units + first;
+      P.nunits = count[L];
+      P.nlimbs = 1;
+      P.logn = (uint32_t)L;
+      P.halving = (uint32_t)halving;
+      P.fused = (uint32_t)fused;
+      P.row_ops = 2;
+      if ((e = pm::launch_polymul_grouped(P, st)) != cudaSuccess)
+        return cuda_fail(e, "grouped uneven launch");
+      first += count[L];
+    }
+    return ok();
   }
   // the three prefix arrays are uploaded contiguously, in the order f, w, i
   if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
@@ -1145,6 +1189,14 @@ pm_status pm_queue_create(pm_queue** out, int device) {
     return cuda_fail(e, "queue setup");
   }
   *out = q;
+  return ok();
+}
+
+pm_status pm_queue_set_mode(pm_queue* q, int mode) {
+  if (!q) return fail(PM_ERR_ARG, "queue is NULL");
+  if (mode < PM_UNEVEN_AUTO || mode > PM_UNEVEN_GROUPED) return fail(PM_ERR_ARG, "mode must be 0..2");
+  std::lock_guard<std::mutex> lk(q->mu);
+  q->mode = mode;
   return ok();
 }
 

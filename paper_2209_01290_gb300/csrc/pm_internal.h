@@ -12,6 +12,8 @@ namespace pm {
 enum Mode { MODE_POLYMUL = 0, MODE_FWD = 1, MODE_INV = 2, MODE_POLYMUL_FUSED = 3 };
 
 // Kernel parameters for one batched call on one plan.
+struct UnitDesc;
+
 struct KParams {
   const uint64_t* a;     // operand a (device), [nunits][N]
   const uint64_t* b;     // operand b
@@ -30,6 +32,8 @@ struct KParams {
   uint32_t word32;       // 1: 32-bit words; a/b/c/s hold uint32_t, twf/twi TwPair32,
                          // lc LimbConst32 (the pointers are reinterpreted)
   uint32_t pad;
+  const UnitDesc* desc;  // grouped launches (64-bit words): unit u's operands, output,
+                         // scratch, tables and constants come from desc[u] instead
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the
@@ -84,6 +88,9 @@ cudaError_t launch_polymul_persistent(const KParams& P, uint32_t* ctl, int grid,
 cudaError_t kernels_prepare();
 cudaError_t launch_polymul(const KParams& P, cudaStream_t st,
                            const PhaseEvents* pe = nullptr);
+// Grouped uneven products (64-bit words): P.desc holds P.nunits unit
+// descriptors of one N (logn >= 12), P.halving / P.fused as for their plans.
+cudaError_t launch_polymul_grouped(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st);
 cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms);

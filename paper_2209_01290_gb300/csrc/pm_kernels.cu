@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 3 : 4) k_rows(KParams P)
 
 // Polymul rows with a and b transformed together in registers (shared
 // twiddle loads, half the barriers per word; 2 CTAs per SM).
-template <bool HALVE, bool FUSED, typename W>
+template <bool HALVE, bool FUSED, typename W, bool DESC = false>
 __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P) {
   extern __shared__ __align__(16) uint64_t smem_raw[];
   W* smem = reinterpret_cast<W*>(smem_raw);
@@ -154,6 +154,16 @@ __global__ void __launch_bounds__(256, sizeof(W) == 8 ? 2 : 3) k_rows2(KParams P
   const uint32_t unit = blockIdx.x >> (logn - kRowLog);
   const uint32_t t = blockIdx.x & ((1u << (logn - kRowLog)) - 1);
   if (unit >= P.nunits) return;
+  if constexpr (DESC) {  // grouped uneven launch: the unit's own pointers
+    static_assert(sizeof(W) == 8, "grouped launches take 64-bit words");
+    const UnitDesc& D = P.desc[unit];
+    const auto K = ld_limb(D.lc);
+    const size_t off = (size_t)t * kRow;
+    const bool single = (logn == kRowLog);
+    row_task_polymul2<HALVE, false>((single ? D.a : D.c) + off, (single ? D.b : D.s) + off,
+                                    D.c + off, single, smem, D.twf, D.twi, K, logn, t, FUSED);
+    return;
+  }
   const uint32_t limb = unit % P.nlimbs;
   const auto K = ld_limb(V.lc + limb);
   const auto* twf = V.twf + ((size_t)limb << logn);
@@ -227,9 +237,32 @@ __global__ void __launch_bounds__(kLatThreads, 1) k_rows_lat(KParams P) {
 // 64 data registers per column otherwise leave 1 CTA per SM (the cap costs a
 // few bytes of spill and gains ~8% at N = 2^17).  An explicit minimum of 1
 // is not the same as none: the compiler then takes more registers.
-template <int R, int S, typename W>
+// With DESC (grouped uneven launches, 64-bit words, S = 1) the unit's
+// pointers come from its descriptor; a square unit (a == b) transforms its
+// operand once (the op-1 thread has nothing to do).
+template <int R, int S, typename W, bool DESC = false>
 __device__ __forceinline__ void col_fwd_body(const KParams& P, int nops) {
   const KView<W> V(P);
+  if constexpr (DESC) {
+    static_assert(S == 1 && sizeof(W) == 8, "grouped launches: 64-bit words, one column per thread");
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (size_t)P.nunits * nops * kRow) return;
+    const uint32_t col = (uint32_t)(id & (kRow - 1));
+    const size_t rest = id >> kRowLog;
+    const uint32_t op = (uint32_t)(rest % nops);
+    const UnitDesc& D = P.desc[rest / nops];
+    if (op == 1 && D.a == D.b) return;
+    const W* src = (op == 0 ? D.a : D.b) + col;
+    W* dst = (op == 0 ? D.c : D.s) + col;
+    W x[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) x[t] = __ldcs(src + (size_t)t * kRow);
+    const auto K = ld_limb(D.lc);
+    ct_col<R>(x, D.twf, K.q, K.two_q);
+#pragma unroll
+    for (int t = 0; t < R; t++) dst[(size_t)t * kRow] = x[t];
+    return;
+  }
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * nops * kRow;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -275,22 +308,37 @@ __device__ __forceinline__ void col_fwd_body(const KParams& P, int nops) {
   }
 }
 
-template <int R, int S, typename W>
+template <int R, int S, typename W, bool DESC = false>
 __global__ void __launch_bounds__(256) k_col_fwd(KParams P, int nops) {
-  col_fwd_body<R, S, W>(P, nops);
+  col_fwd_body<R, S, W, DESC>(P, nops);
 }
 
-template <int R, int S, typename W>
+template <int R, int S, typename W, bool DESC = false>
 __global__ void __launch_bounds__(256, 2) k_col_fwd_cap(KParams P, int nops) {
-  col_fwd_body<R, S, W>(P, nops);
+  col_fwd_body<R, S, W, DESC>(P, nops);
 }
 
 // Inverse column stages (the last log2 R stages of Algorithm 7) plus the
 // reduction to [0, q); in place on c.  S columns per thread, software
 // pipelined as in k_col_fwd.
-template <int R, int S, bool HALVE, typename W>
+template <int R, int S, bool HALVE, typename W, bool DESC = false>
 __device__ __forceinline__ void col_inv_body(const KParams& P) {
   const KView<W> V(P);
+  if constexpr (DESC) {
+    static_assert(S == 1 && sizeof(W) == 8, "grouped launches: 64-bit words, one column per thread");
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (size_t)P.nunits * kRow) return;
+    const UnitDesc& D = P.desc[id >> kRowLog];
+    W* p = D.c + (id & (kRow - 1));
+    W x[R];
+#pragma unroll
+    for (int t = 0; t < R; t++) x[t] = p[(size_t)t * kRow];
+    const auto K = ld_limb(D.lc);
+    gs_col<R, HALVE>(x, D.twi, K);
+#pragma unroll
+    for (int t = 0; t < R; t++) __stcs(p + (size_t)t * kRow, csub(x[t], K.q));
+    return;
+  }
   const uint32_t logn = P.logn;
   const size_t total = (size_t)P.nunits * kRow;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -331,14 +379,14 @@ __device__ __forceinline__ void col_inv_body(const KParams& P) {
   }
 }
 
-template <int R, int S, bool HALVE, typename W>
+template <int R, int S, bool HALVE, typename W, bool DESC = false>
 __global__ void __launch_bounds__(256) k_col_inv(KParams P) {
-  col_inv_body<R, S, HALVE, W>(P);
+  col_inv_body<R, S, HALVE, W, DESC>(P);
 }
 
-template <int R, int S, bool HALVE, typename W>
+template <int R, int S, bool HALVE, typename W, bool DESC = false>
 __global__ void __launch_bounds__(256, 2) k_col_inv_cap(KParams P) {
-  col_inv_body<R, S, HALVE, W>(P);
+  col_inv_body<R, S, HALVE, W, DESC>(P);
 }
 
 // N = 2^13 in one CTA of 512 threads: 2 rows.  The single column stage
@@ -673,6 +721,8 @@ static cudaError_t prepare_mode() {
                             (const void*)k_rows<MODE_POLYMUL_FUSED, H, W>,
                             (const void*)k_rows2<H, false, W>,
                             (const void*)k_rows2<H, true, W>,
+                            (const void*)k_rows2<H, false, W, sizeof(W) == 8>,
+                            (const void*)k_rows2<H, true, W, sizeof(W) == 8>,
                             (const void*)k_rows<MODE_FWD, H, W>,
                             (const void*)k_rows<MODE_INV, H, W>};
   const void* lat_fns[] = {(const void*)k_rows_lat<MODE_POLYMUL, H, W>,
@@ -779,6 +829,63 @@ static cudaError_t launch_ntt_inv_w(const KParams& P, cudaStream_t st) {
   cudaError_t e = rows<MODE_INV, W>(P, st);
   if (e != cudaSuccess || P.logn == 12) return e;
   return col_inv<W>(P, st);
+}
+
+// Grouped uneven launch (64-bit words): all units of one N, pointers from
+// P.desc; the column stages one column per thread, the two-operand rows.
+template <int R>
+static cudaError_t polymul_desc_r(const KParams& P, cudaStream_t st) {
+  using W = uint64_t;
+  const unsigned rows = P.nunits << (P.logn - kRowLog);
+  if constexpr (R > 1) {
+    const unsigned fb = (unsigned)(((size_t)P.nunits * 2 * kRow + 255) / 256);
+    if constexpr (R == 32)
+      k_col_fwd_cap<R, 1, W, true><<<fb, 256, 0, st>>>(P, 2);
+    else
+      k_col_fwd<R, 1, W, true><<<fb, 256, 0, st>>>(P, 2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (P.halving) {
+    if (P.fused)
+      k_rows2<true, true, W, true><<<rows, 256, kRowsSmem<W>, st>>>(P);
+    else
+      k_rows2<true, false, W, true><<<rows, 256, kRowsSmem<W>, st>>>(P);
+  } else {
+    if (P.fused)
+      k_rows2<false, true, W, true><<<rows, 256, kRowsSmem<W>, st>>>(P);
+    else
+      k_rows2<false, false, W, true><<<rows, 256, kRowsSmem<W>, st>>>(P);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || R == 1) return e;
+  const unsigned ib = (unsigned)(((size_t)P.nunits * kRow + 255) / 256);
+  if constexpr (R == 32) {
+    if (P.halving)
+      k_col_inv_cap<R, 1, true, W, true><<<ib, 256, 0, st>>>(P);
+    else
+      k_col_inv_cap<R, 1, false, W, true><<<ib, 256, 0, st>>>(P);
+  } else if constexpr (R > 1) {
+    if (P.halving)
+      k_col_inv<R, 1, true, W, true><<<ib, 256, 0, st>>>(P);
+    else
+      k_col_inv<R, 1, false, W, true><<<ib, 256, 0, st>>>(P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_polymul_grouped(const KParams& P, cudaStream_t st) {
+  if (P.nunits == 0) return cudaSuccess;
+  if (P.word32 || !P.desc) return cudaErrorInvalidValue;
+  switch (P.logn) {
+    case 12: return polymul_desc_r<1>(P, st);
+    case 13: return polymul_desc_r<2>(P, st);
+    case 14: return polymul_desc_r<4>(P, st);
+    case 15: return polymul_desc_r<8>(P, st);
+    case 16: return polymul_desc_r<16>(P, st);
+    case 17: return polymul_desc_r<32>(P, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 static unsigned grid_cap(size_t blocks, int num_sms) {

@@ -150,12 +150,13 @@ def test_fused_graph(oracle):
     assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis))
 
 
-def test_fused_uneven(oracle):
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "grouped"])
+def test_fused_uneven(oracle, mode):
     """An uneven batch of fused plans; mixing fused and default plans of
     N >= 4096 in one launch is rejected."""
     from paper_2209_01290_gb300 import Plan, Queue, capi
     shapes = [(12, 2), (16, 1), (13, 3), (5, 2), (14, 2), (17, 1)]
-    q = Queue()
+    q = Queue(mode=mode)
     jobs, data = [], []
     for j, (log2n, L) in enumerate(shapes):
         plan, qs, psis = _plan(log2n, L)

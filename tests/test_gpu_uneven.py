@@ -22,11 +22,16 @@ def _plans(shapes, halving=False):
     return out
 
 
-def test_uneven_mixed_sizes(oracle):
+MODES = [0, 1, 2]
+MODE_IDS = ["auto", "persistent", "grouped"]
+
+
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_uneven_mixed_sizes(oracle, mode):
     from paper_2209_01290_gb300 import Queue
     shapes = [(12, 3), (17, 1), (13, 2), (3, 2), (16, 2), (14, 4), (15, 1), (12, 1), (16, 1)]
     plans = _plans(shapes)
-    q = Queue()
+    q = Queue(mode=mode)
     jobs, data = [], []
     for j, ((plan, qs, psis), (log2n, L)) in enumerate(zip(plans, shapes)):
         P = 2 if log2n <= 14 else 1
@@ -42,11 +47,12 @@ def test_uneven_mixed_sizes(oracle):
             assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis))
 
 
-def test_uneven_aliasing(oracle):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_uneven_aliasing(oracle, mode):
     from paper_2209_01290_gb300 import Queue
     shapes = [(14, 2), (16, 1), (13, 2), (12, 2)]
     plans = _plans(shapes)
-    q = Queue()
+    q = Queue(mode=mode)
     jobs, checks = [], []
     for j, ((plan, qs, psis), (log2n, L)) in enumerate(zip(plans, shapes)):
         a, b = operands(21000 + j, qs, 1, 1 << log2n)
@@ -78,7 +84,8 @@ def test_uneven_rejects_mixed_halving():
     assert e.value.status == -1
 
 
-def test_uneven_halving_plans(oracle):
+@pytest.mark.parametrize("mode", MODES, ids=MODE_IDS)
+def test_uneven_halving_plans(oracle, mode):
     from paper_2209_01290_gb300 import Queue
     shapes = [(13, 1), (17, 1), (12, 2)]
     plans = _plans(shapes, halving=True)
@@ -89,15 +96,24 @@ def test_uneven_halving_plans(oracle):
         dc = da.new_empty(da.shape)
         jobs.append((plan, da, db, dc))
         data.append((a, b, qs, psis, dc))
-    q = Queue()
+    q = Queue(mode=mode)
     q.polymul_uneven(jobs)
     q.sync()
     for a, b, qs, psis, dc in data:
         assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis))
 
 
+def test_uneven_mode_checks():
+    from paper_2209_01290_gb300 import Queue, capi
+    q = Queue()
+    for bad in (-1, 3):
+        with pytest.raises(capi.PMError):
+            capi.pm_queue_set_mode(q._h, bad)
+
+
 @pytest.mark.slow
-def test_c4_full_uneven_batch_sampled(oracle):
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "grouped"])
+def test_c4_full_uneven_batch_sampled(oracle, mode):
     """The full uneven configuration: 512 jobs, N uniform over 2^12..2^17,
     1..48 limbs (the largest primes = 1 mod 2N), inputs generated on the
     device; one launch; 24 sampled (job, limb) units checked in full against
@@ -118,7 +134,7 @@ def test_c4_full_uneven_batch_sampled(oracle):
         c = torch.empty_like(a)
         jobs.append((plan, a, b, c))
         meta.append((qs, psis))
-    q = Queue()
+    q = Queue(mode=mode)
     q.polymul_uneven(jobs)
     q.sync()
     rng = np.random.default_rng(9)
