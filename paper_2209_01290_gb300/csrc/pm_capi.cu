@@ -829,7 +829,7 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
   if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
     return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
-  if (t->row_ops > 3) return fail(PM_ERR_ARG, "row_ops must be 0..3");
+  if (t->row_ops > 4) return fail(PM_ERR_ARG, "row_ops must be 0..4");
   if (t->variant == PM_VARIANT_PERSISTENT && is_word32(plan))
     return fail(PM_ERR_ARG, "the persistent variant takes 64-bit plans");
   if (t->variant == PM_VARIANT_PERSISTENT &&
@@ -857,6 +857,7 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
     cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 3});
   }
+  if (pm::wide_polymul_ok(plan->logn)) cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 4});
   if (plan->logn >= 13 && !is_word32(plan)) {
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});

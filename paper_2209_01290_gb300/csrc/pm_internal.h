@@ -26,7 +26,8 @@ struct KParams {
   uint32_t nlimbs;
   uint32_t nunits;       // npoly * nlimbs
   uint32_t halving;      // 1: per-stage 1/2 scaling (table holds w/2); 0: 1/N folded at the end
-  uint32_t row_ops;      // polymul row kernel: 1 = operands one after the other, 2 = together
+  uint32_t row_ops;      // row kernel: 1 = operands one after the other, 2 = together,
+                         // 3 = 1024 threads per 4096-word row, 4 = 1024-word rows
   uint32_t fused;        // polymul by Algorithm 8; lc then has 2 nlimbs entries, the second
                          // half (2/N in place of 1/N) used by the polymul launchers
   uint32_t word32;       // 1: 32-bit words; a/b/c/s hold uint32_t, twf/twi TwPair32,
@@ -94,6 +95,17 @@ cudaError_t launch_polymul_grouped(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st);
 cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms);
+
+// The latency split (pm_wide.cu): rows of 1024 words, chosen with row_ops 4,
+// for N = 2^10 .. 2^17: one launch up to N = 2^13 (a thread-block cluster
+// per unit above 2^10, no scratch), three from 2^14 (the [nunits][N] scratch
+// of the 4096-word split).
+bool wide_polymul_ok(uint32_t logn);
+bool wide_ntt_ok(uint32_t logn);
+cudaError_t wide_prepare();
+cudaError_t launch_polymul_wide(const KParams& P, cudaStream_t st, const PhaseEvents* pe);
+cudaError_t launch_ntt_fwd_wide(const KParams& P, cudaStream_t st);
+cudaError_t launch_ntt_inv_wide(const KParams& P, cudaStream_t st);
 cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st, int num_sms);
 
 // True when the polymul path for this N needs the [nunits][N] scratch.

@@ -42,28 +42,6 @@
 namespace pm {
 
 // ------------------------------------------------------------------ kernels
-// Every kernel is a template over the word type W (W: q < 2^62;
-// uint32_t: q < 2^30); KParams carries untyped device pointers and KView<W>
-// gives the typed views.
-
-template <typename W>
-struct KView {
-  const W* a;
-  const W* b;
-  W* c;
-  W* s;
-  const typename WordT<W>::Tw* twf;
-  const typename WordT<W>::Tw* twi;
-  const typename WordT<W>::LC* lc;
-  __device__ __forceinline__ explicit KView(const KParams& P)
-      : a(reinterpret_cast<const W*>(P.a)),
-        b(reinterpret_cast<const W*>(P.b)),
-        c(reinterpret_cast<W*>(P.c)),
-        s(reinterpret_cast<W*>(P.s)),
-        twf(reinterpret_cast<const typename WordT<W>::Tw*>(P.twf)),
-        twi(reinterpret_cast<const typename WordT<W>::Tw*>(P.twi)),
-        lc(reinterpret_cast<const typename WordT<W>::LC*>(P.lc)) {}
-};
 
 // 16 consecutive words of a row (16-byte aligned) in or out with 16-byte
 // accesses; the store reduces [0, 4q) -> [0, q).
@@ -747,6 +725,7 @@ static cudaError_t prepare_mode() {
 // device (once per device, before the first launch).
 cudaError_t kernels_prepare() {
   cudaError_t e;
+  if ((e = wide_prepare()) != cudaSuccess) return e;
   if ((e = prepare_mode<false, uint64_t>()) != cudaSuccess) return e;
   if ((e = prepare_mode<true, uint64_t>()) != cudaSuccess) return e;
   if ((e = prepare_mode<false, uint32_t>()) != cudaSuccess) return e;
@@ -894,14 +873,17 @@ static unsigned grid_cap(size_t blocks, int num_sms) {
 }
 
 cudaError_t launch_polymul(const KParams& P, cudaStream_t st, const PhaseEvents* pe) {
+  if (P.row_ops == 4 && wide_polymul_ok(P.logn)) return launch_polymul_wide(P, st, pe);
   return P.word32 ? launch_polymul_w<uint32_t>(P, st, pe) : launch_polymul_w<uint64_t>(P, st, pe);
 }
 
 cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st) {
+  if (P.row_ops == 4 && wide_ntt_ok(P.logn)) return launch_ntt_fwd_wide(P, st);
   return P.word32 ? launch_ntt_fwd_w<uint32_t>(P, st) : launch_ntt_fwd_w<uint64_t>(P, st);
 }
 
 cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st) {
+  if (P.row_ops == 4 && wide_ntt_ok(P.logn)) return launch_ntt_inv_wide(P, st);
   return P.word32 ? launch_ntt_inv_w<uint32_t>(P, st) : launch_ntt_inv_w<uint64_t>(P, st);
 }
 

@@ -273,6 +273,29 @@ __device__ __forceinline__ LimbConst32 ld_limb(const LimbConst32* __restrict__ p
   return k;
 }
 
+// Kernels are templates over the word type W (uint64_t: q < 2^62;
+// uint32_t: q < 2^30); KParams carries untyped device pointers and KView<W>
+// gives the typed views.
+
+template <typename W>
+struct KView {
+  const W* a;
+  const W* b;
+  W* c;
+  W* s;
+  const typename WordT<W>::Tw* twf;
+  const typename WordT<W>::Tw* twi;
+  const typename WordT<W>::LC* lc;
+  __device__ __forceinline__ explicit KView(const KParams& P)
+      : a(reinterpret_cast<const W*>(P.a)),
+        b(reinterpret_cast<const W*>(P.b)),
+        c(reinterpret_cast<W*>(P.c)),
+        s(reinterpret_cast<W*>(P.s)),
+        twf(reinterpret_cast<const typename WordT<W>::Tw*>(P.twf)),
+        twi(reinterpret_cast<const typename WordT<W>::Tw*>(P.twi)),
+        lc(reinterpret_cast<const typename WordT<W>::LC*>(P.lc)) {}
+};
+
 // ----------------------------------------------------------- row pipeline
 
 // The 12 in-row stages of one 4096-word row (row t of a unit of 2^logn

@@ -22,8 +22,9 @@ def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None):
     return plan, qs, psis
 
 
-@pytest.mark.parametrize("variant", [(0, 1), (0, 2), (0, 3), (1, 1)],
-                         ids=["split-rows1", "split-rows2", "split-rowslat", "persistent"])
+@pytest.mark.parametrize("variant", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 1)],
+                         ids=["split-rows1", "split-rows2", "split-rowslat", "split-wide",
+                              "persistent"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold2N", "halving"])
 @pytest.mark.parametrize("log2n", FUSED_LOG2N)
 def test_fused_all_sizes(oracle, log2n, halving, variant):

@@ -30,8 +30,8 @@ def _plan(log2n, nlimbs, qbits=60, halving=False, variant=None):
     return plan, qs, psis
 
 
-VARIANTS = [(0, 1), (0, 2), (0, 3), (1, 1)]
-VARIANT_IDS = ["split-rows1", "split-rows2", "split-rowslat", "persistent"]
+VARIANTS = [(0, 1), (0, 2), (0, 3), (0, 4), (1, 1)]
+VARIANT_IDS = ["split-rows1", "split-rows2", "split-rowslat", "split-wide", "persistent"]
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=VARIANT_IDS)
@@ -41,7 +41,8 @@ def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving, variant):
     """Every code path: radix-2 smem kernel (N <= 2^11), single-row kernel
     (2^12), one-CTA 2^13 kernel, column split (2^14..2^17) as three launches
     (row kernel with the operands one after the other, together, or over
-    1024 threads in radix-4 passes) or as one persistent work-queue launch
+    1024 threads in radix-4 passes), the 1024-word-row split (N >= 2^10:
+    one cluster launch up to 2^13) or one persistent work-queue launch
     (2^13..2^17); 2 polys x 3 limbs; 1/N folded into the last stage or
     applied as per-stage halving."""
     n = 1 << log2n
@@ -54,15 +55,16 @@ def test_polymul_all_sizes(torch_cuda, oracle, log2n, halving, variant):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("row_ops", [0, 1, 3], ids=["auto", "rows1", "rowslat"])
+@pytest.mark.parametrize("row_ops", [0, 1, 3, 4], ids=["auto", "rows1", "rowslat", "wide"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold1N", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
 def test_ntt_fwd_inv_all_sizes(torch_cuda, oracle, log2n, halving, row_ops):
     """Forward NTT equals the oracle's bo-order transform; inverse equals the
     oracle's inverse; inverse(forward(x)) = x.  Row kernels for N >= 4096:
-    by batch size, 256 threads per row, 1024 threads per row."""
-    if row_ops and log2n < 12:
-        pytest.skip("no in-row kernel below N = 4096")
+    by batch size, 256 threads per row, 1024 threads per row; 1024-word rows
+    for N >= 1024."""
+    if row_ops and log2n < (10 if row_ops == 4 else 12):
+        pytest.skip("no in-row kernel of this kind at this N")
     n = 1 << log2n
     L = 2
     plan, qs, psis = _plan(log2n, L, halving=halving, variant=(0, row_ops) if row_ops else None)

@@ -1,0 +1,164 @@
+"""The 1024-word-row latency split (row_ops 4): bit-exact against the CPU
+oracle at every size it serves (N = 2^10 .. 2^17: one row kernel at 2^10,
+one cluster launch per batch at 2^11 .. 2^13, three launches from 2^14),
+both word types, Eq. 2 and Algorithm 8, both scaling modes, plus aliasing,
+edge inputs, moduli near the word limits, larger batches, CUDA graph
+capture and the allocation-free entry point."""
+import numpy as np
+import pytest
+
+from helpers import operands, oracle_polymul_batch, schoolbook_coeff, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+WIDE_POLYMUL = [10, 11, 12, 13, 14, 15, 16, 17]
+
+
+def _plan(log2n, nlimbs, qbits=60, halving=False, fused=False):
+    from paper_2209_01290_gb300 import Plan, capi
+    qs, psis = capi.pm_find_params(log2n, nlimbs, qbits)
+    plan = Plan(1 << log2n, qs, psis, halving=halving, fused=fused)
+    capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=4)
+    return plan, qs, psis
+
+
+@pytest.mark.parametrize("fused", [False, True], ids=["eq2", "alg8"])
+@pytest.mark.parametrize("halving", [False, True], ids=["fold", "halving"])
+@pytest.mark.parametrize("log2n", WIDE_POLYMUL)
+def test_wide_polymul_batches(oracle, log2n, halving, fused):
+    """Several polynomials and limbs in one launch: every unit in full."""
+    n = 1 << log2n
+    L, P = (4, 3) if log2n <= 15 else (3, 2)
+    plan, qs, psis = _plan(log2n, L, halving=halving, fused=fused)
+    a, b = operands(70000 + log2n, qs, P, n)
+    got = to_host(plan.polymul(to_dev(a), to_dev(b)))
+    assert np.array_equal(got, oracle_polymul_batch(oracle, a, b, qs, psis))
+
+
+@pytest.mark.parametrize("fused", [False, True], ids=["eq2", "alg8"])
+@pytest.mark.parametrize("log2n", WIDE_POLYMUL)
+def test_wide_aliasing(oracle, log2n, fused):
+    """c may alias a or b; a == b (squaring, one column transform)."""
+    n = 1 << log2n
+    plan, qs, psis = _plan(log2n, 2, fused=fused)
+    a, b = operands(71000 + log2n, qs, 1, n)
+    want = oracle_polymul_batch(oracle, a, b, qs, psis)
+    want_sq = oracle_polymul_batch(oracle, a, a, qs, psis)
+    da, db = to_dev(a), to_dev(b)
+    plan.polymul(da, db, out=da)
+    assert np.array_equal(to_host(da), want)
+    da, db = to_dev(a), to_dev(b)
+    plan.polymul(da, db, out=db)
+    assert np.array_equal(to_host(db), want)
+    da = to_dev(a)
+    assert np.array_equal(to_host(plan.polymul(da, da)), want_sq)
+    plan.polymul(da, da, out=da)
+    assert np.array_equal(to_host(da), want_sq)
+
+
+@pytest.mark.parametrize("log2n", WIDE_POLYMUL)
+def test_wide_edges(oracle, log2n):
+    """Zeros, maximal words (all q - 1), monomials across the X^N = -1 wrap,
+    sampled schoolbook coefficients."""
+    n = 1 << log2n
+    plan, qs, psis = _plan(log2n, 1)
+    q = qs[0]
+    z = np.zeros((1, 1, n), np.uint64)
+    full = np.full((1, 1, n), q - 1, np.uint64)
+    assert not to_host(plan.polymul(to_dev(z), to_dev(full))).any()
+    got = to_host(plan.polymul(to_dev(full), to_dev(full)))
+    assert np.array_equal(got[0, 0], np.array([(2 * k + 2 - n) % q for k in range(n)], np.uint64))
+    rng = np.random.default_rng(log2n)
+    for i, j in [(0, 0), (n - 1, n - 1), (n - 1, 1), (1023, 1), tuple(rng.integers(0, n, 2))]:
+        a = np.zeros((1, 1, n), np.uint64)
+        b = np.zeros((1, 1, n), np.uint64)
+        a[0, 0, i] = 1
+        b[0, 0, j] = 1
+        want = np.zeros(n, np.uint64)
+        if i + j < n:
+            want[i + j] = 1
+        else:
+            want[i + j - n] = q - 1
+        assert np.array_equal(to_host(plan.polymul(to_dev(a), to_dev(b)))[0, 0], want), (i, j)
+    a, b = operands(72000 + log2n, qs, 1, n)
+    got = to_host(plan.polymul(to_dev(a), to_dev(b)))
+    for k in rng.integers(0, n, 3):
+        assert int(got[0, 0, k]) == schoolbook_coeff(a[0, 0], b[0, 0], q, int(k))
+
+
+@pytest.mark.parametrize("qbits,log2n", [(62, 10), (62, 12), (62, 16), (30, 13), (30, 14), (40, 17)])
+def test_wide_word_sizes(oracle, qbits, log2n):
+    """Moduli at the top of the 64-bit range (lazy words up to 4q < 2^64)
+    and small ones in 64-bit words."""
+    n = 1 << log2n
+    plan, qs, psis = _plan(log2n, 2, qbits=qbits)
+    a, b = operands(73000 + log2n + qbits, qs, 1, n)
+    got = to_host(plan.polymul(to_dev(a), to_dev(b)))
+    assert np.array_equal(got, oracle_polymul_batch(oracle, a, b, qs, psis))
+    d = to_dev(a)
+    plan.ntt_fwd_(d)
+    fwd = to_host(d)
+    for l in range(2):
+        assert np.array_equal(fwd[0, l], oracle.ntt_fwd_bo(a[0, l], qs[l], psis[l])), l
+    plan.ntt_inv_(d)
+    assert np.array_equal(to_host(d), a)
+
+
+@pytest.mark.parametrize("log2n", [10, 12, 14, 17])
+def test_wide_graph(oracle, log2n):
+    """A polymul captured with the wide tuning replays bit-exactly after the
+    inputs change."""
+    plan, qs, psis = _plan(log2n, 2)
+    a, b = operands(74000 + log2n, qs, 2, 1 << log2n)
+    da, db = to_dev(a), to_dev(b)
+    dc = da.new_empty(da.shape)
+    g = plan.graph_polymul(da, db, dc)
+    for rep in range(2):
+        if rep:
+            a, b = operands(74100 + log2n, qs, 2, 1 << log2n)
+            da.copy_(to_dev(a))
+            db.copy_(to_dev(b))
+        g.launch()
+        plan.sync()
+        assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis)), rep
+    g.close()
+
+
+@pytest.mark.parametrize("log2n", [10, 13, 14, 16])
+def test_wide_noalloc(oracle, log2n):
+    import torch
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis = _plan(log2n, 2)
+    a, b = operands(75000 + log2n, qs, 2, 1 << log2n)
+    da, db = to_dev(a), to_dev(b)
+    dc = torch.empty_like(da)
+    capi.pm_polymul_noalloc(plan.handle, da.data_ptr(), db.data_ptr(), dc.data_ptr(), 2,
+                            torch.cuda.current_stream().cuda_stream)
+    assert np.array_equal(to_host(dc), oracle_polymul_batch(oracle, a, b, qs, psis))
+
+
+def test_wide_phase_events():
+    """The profiling hook records one event per launch of the split."""
+    import torch
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis = _plan(16, 1)
+    a, b = operands(76000, qs, 1, 1 << 16)
+    da, db = to_dev(a), to_dev(b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record()  # torch creates the CUDA event at its first record
+    torch.cuda.synchronize()
+    capi.pm_plan_set_phase_events(plan.handle, [e.cuda_event for e in ev])
+    plan.polymul(da, db)
+    capi.pm_plan_set_phase_events(plan.handle, [])
+    torch.cuda.synchronize()
+    assert all(ev[k].elapsed_time(ev[k + 1]) >= 0 for k in range(3))
+
+
+def test_wide_tuning_range():
+    from paper_2209_01290_gb300 import capi
+    plan, *_ = _plan(14, 1)
+    assert capi.pm_plan_get_tuning(plan.handle).row_ops == 4
+    with pytest.raises(capi.PMError) as e:
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=5)
+    assert e.value.status == -1

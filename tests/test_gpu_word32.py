@@ -31,7 +31,7 @@ def _plan(log2n, nlimbs, qbits=30, halving=False, fused=False, row_ops=None):
     return plan, qs, psis
 
 
-@pytest.mark.parametrize("row_ops", [1, 2, 3], ids=["rows1", "rows2", "rowslat"])
+@pytest.mark.parametrize("row_ops", [1, 2, 3, 4], ids=["rows1", "rows2", "rowslat", "wide"])
 @pytest.mark.parametrize("fused", [False, True], ids=["eq2", "alg8"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
@@ -49,12 +49,13 @@ def test_polymul32_all_sizes(oracle, log2n, halving, fused, row_ops):
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("row_ops", [1, 3], ids=["rows1", "rowslat"])
+@pytest.mark.parametrize("row_ops", [1, 3, 4], ids=["rows1", "rowslat", "wide"])
 @pytest.mark.parametrize("halving", [False, True], ids=["fold", "halving"])
 @pytest.mark.parametrize("log2n", ALL_LOG2N)
 def test_ntt32_fwd_inv_all_sizes(oracle, log2n, halving, row_ops):
     n = 1 << log2n
-    plan, qs, psis = _plan(log2n, 2, halving=halving, row_ops=row_ops if log2n >= 12 else None)
+    plan, qs, psis = _plan(log2n, 2, halving=halving,
+                           row_ops=row_ops if log2n >= (10 if row_ops == 4 else 12) else None)
     x, y = operands(61000 + log2n, qs, 1, n)
     d = to_dev32(x)
     plan.ntt_fwd_(d)
