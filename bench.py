@@ -44,13 +44,25 @@ def mulmods_per_polymul(log2n: int) -> int:
     return 3 * (n // 2) * log2n + n
 
 
-def rows_kernel_mulmods(log2n: int) -> int:
+def rows_kernel_mulmods(log2n: int, row_log: int = 12) -> int:
     """Modular products done by the row kernel of the split path for one unit:
-    12 forward in-row stages on a and b, the pointwise product and 12 inverse
-    in-row stages."""
+    the in-row forward stages on a and b (12 for rows of 4096 words, 10 for
+    rows of 1024), the pointwise product and as many inverse in-row stages."""
     n = 1 << log2n
-    rows_stages = min(12, log2n)
+    rows_stages = min(row_log, log2n)
     return 2 * rows_stages * (n // 2) + n + rows_stages * (n // 2)
+
+
+def auto_row_ops(log2n: int, units: int, sms: int, word32: bool = False) -> int:
+    """The library's row kernel for row_ops 0 (pm.h): rows of 1024 words
+    (4) for 64-bit words except N = 2^12 batches above 64 units, and for
+    32-bit words in batches of up to 2^20 words; otherwise 4096-word rows
+    (3 up to one row per SM, else 2)."""
+    wide = log2n >= 10 and ((units << log2n) <= (1 << 20) if word32
+                            else not (log2n == 12 and units > 64))
+    if wide:
+        return 4
+    return 3 if (units << max(log2n - 12, 0)) <= sms else 2
 
 
 class ClockSampler:
@@ -307,16 +319,19 @@ def run_gpu(args):
     elif log2n >= 14:
         dom_idx = 1
         row_ops = tuning.row_ops
-        if row_ops == 0:  # the library's choice by batch size
+        if row_ops == 0:  # the library's choice by N and batch size
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            row_ops = 3 if (units << (log2n - 12)) <= sms else 2
+            row_ops = auto_row_ops(log2n, units, sms)
         dom_name = {2: "k_rows2<POLYMUL> (in-row stages of a and b together, Barrett pointwise, "
                        "inverse in-row stages)",
                     3: "k_rows_lat<POLYMUL> (1024 threads per row, radix-4 passes)",
-                    1: "k_rows<POLYMUL> (in-row stages + Barrett pointwise)"}[row_ops]
-        dom_mulmods = rows_kernel_mulmods(log2n) * units
+                    1: "k_rows<POLYMUL> (in-row stages + Barrett pointwise)",
+                    4: "k_wrows<POLYMUL> (1024-word rows: 10 in-row stages of a and b in "
+                       "radix-4 passes, Barrett pointwise, 10 inverse in-row stages; row "
+                       "twiddles staged in shared memory)"}[row_ops]
+        dom_mulmods = rows_kernel_mulmods(log2n, 10 if row_ops == 4 else 12) * units
     else:
-        dom_idx, dom_name = 0, "fused single-kernel polymul"
+        dom_idx, dom_name = 0, "single-launch polymul"
         dom_mulmods = mulmods_per_polymul(log2n) * units
     dom_ms = avg_phase[dom_idx]
     achieved = dom_mulmods / (dom_ms * 1e-3)

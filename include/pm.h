@@ -316,25 +316,36 @@ pm_status pm_server_get_stats(pm_server *s, pm_server_stats *out);
 pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t npoly,
                            void *stream);
 
-/* How pm_polymul is launched for N >= 2^13 (a performance choice only; the
- * results are identical):
- *   PM_VARIANT_SPLIT      : three launches -- forward column stages, in-row
+/* How pm_polymul is launched (a performance choice only; the results are
+ * identical):
+ *   PM_VARIANT_SPLIT      : the transform split into rows and columns: up to
+ *                           three launches -- forward column stages, in-row
  *                           stages with the pointwise product, inverse column
- *                           stages (N = 2^13: one launch);
+ *                           stages (row kernel and row length: row_ops);
  *   PM_VARIANT_PERSISTENT : one persistent launch whose CTAs take column and
  *                           row tasks of all units from a work queue in a
  *                           software-pipelined order (lag_fwd / lag_inv are
  *                           the pipeline distances in units, ctas_per_sm the
  *                           resident CTAs per SM).  Uses a control block of
  *                           16 + 8 * units bytes in the stream's scratch.
- * row_ops (SPLIT only; the in-row stages of N >= 4096):
+ * row_ops (SPLIT only):
+ *   1..3: the transform as rows of 4096 words (N >= 4096):
  *   1 = 256 threads per row, a transformed before b (3 CTAs per SM);
  *   2 = 256 threads per row, a and b together sharing twiddle loads
- *       (2 CTAs per SM) -- the throughput kernel;
- *   3 = 1024 threads per row in radix-4 passes (1 CTA per SM) -- for
- *       batches too small to fill the GPU (also used by pm_ntt_fwd/inv);
- *   0 = by batch size: 3 while the batch has at most (SM count) rows of
- *       4096 words, else 2 (pm_ntt_fwd/inv: 3, else 1).
+ *       (2 CTAs per SM);
+ *   3 = 1024 threads per row in radix-4 passes (1 CTA per SM);
+ *   4 = the transform as N/1024 rows of 1024 words (N >= 1024): 256
+ *       threads per row in radix-4 passes with the row's twiddles staged in
+ *       shared memory, up to 4 CTAs per SM; for N = 2^11 .. 2^13 one launch
+ *       (a thread-block cluster of N/1024 CTAs per unit exchanging the
+ *       column stages through distributed shared memory, no scratch), from
+ *       2^14 three launches (column stages, rows, column stages);
+ *   0 = by N, word size and batch size (measured on GB300): 4 for 64-bit
+ *       words, except N = 2^12 batches above 64 units; 4 for 32-bit words
+ *       in batches of up to 2^20 words; otherwise 3 while the batch has at
+ *       most (SM count) rows of 4096 words, else 2 (pm_ntt_fwd/inv: 1).
+ *   Sizes a choice does not cover keep their own kernels (N <= 2^11 without
+ *   4: one CTA per unit; N = 2^13 without 4: one CTA of 512 threads).
  * pm_plan_autotune() picks these by timing; without it a plan uses SPLIT,
  * row_ops 0 (persistent settings: 3 CTAs per SM, lags 8 and 64). */
 enum { PM_VARIANT_SPLIT = 0, PM_VARIANT_PERSISTENT = 1 };

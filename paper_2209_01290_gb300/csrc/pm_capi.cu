@@ -143,11 +143,18 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.nlimbs = p->nlimbs;
   P.nunits = npoly * p->nlimbs;
   P.halving = (p->flags & PM_PLAN_HALVING) ? 1 : 0;
-  // row kernel: 1 = k_rows, 2 = k_rows2, 3 = k_rows_lat; 0 = by batch size:
-  // the 1024-thread latency rows while the batch has at most one row per SM
-  // (measured faster there), the two-operand throughput rows above
+  // row kernel: 1 = k_rows, 2 = k_rows2, 3 = k_rows_lat, 4 = the 1024-word
+  // rows of pm_wide.cu; 0 = by N, word size and batch size, as measured on
+  // GB300: the 1024-word rows for 64-bit words at every N >= 2^10 except
+  // N = 2^12 batches above 64 units, and for 32-bit words in batches of up
+  // to 2^20 words; otherwise the 4096-word rows, the 1024-thread latency
+  // rows up to one row per SM and the two-operand throughput rows above
+  const uint64_t words = (uint64_t)P.nunits << p->logn;
+  const bool wide = p->logn >= 10 && (is_word32(p) ? words <= (1ull << 20)
+                                                   : !(p->logn == 12 && P.nunits > 64));
   const uint64_t row_ctas = p->logn >= 12 ? (uint64_t)P.nunits << (p->logn - 12) : 0;
   P.row_ops = p->tune.row_ops ? p->tune.row_ops
+              : wide          ? 4u
                               : (row_ctas <= (uint64_t)p->num_sms ? 3u : 2u);
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
   P.word32 = is_word32(p) ? 1 : 0;
