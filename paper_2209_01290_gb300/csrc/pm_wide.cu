@@ -97,8 +97,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Row t's twiddles of one table into shared memory.  Forward in-row stage r
 // (global stage n-10+r) uses the 2^r entries Psi_br[2^(n-10+r) + t 2^r + i],
 // i < 2^r; inverse GS stage 9-r uses Psi^-1_br at the same indices (GS stage
-// sig has N/2^(sig+1) blocks, row t's are t 2^(9-sig) ...).  Slice r is
-// staged at dst[2^r - 1 + i].
+// sig has N/2^(sig+1) blocks, row t's are t 2^(9-sig) ...).  Slice r starts
+// at dst[2^r - 1].  Even slices hold entry i at position i; odd slices, which
+// the passes read in pairs (2 blk, 2 blk + 1), hold the even entries first
+// and the odd ones after them (entry i at (i & 1) 2^(r-1) + i/2), so that
+// threads with consecutive blk read consecutive positions in both halves
+// (no bank conflicts in the block-fastest passes).
 template <typename W>
 __device__ __forceinline__ void w_stage_tw(typename WordT<W>::Tw* dst,
                                            const typename WordT<W>::Tw* __restrict__ tw,
@@ -109,8 +113,10 @@ __device__ __forceinline__ void w_stage_tw(typename WordT<W>::Tw* dst,
     const int i = th + k * kWThreads;
     if (i < kWTw - 1) {
       const int r = 31 - __clz(i + 1);
-      const uint32_t idx = (1u << (logn - kWLog + r)) + (t << r) + (uint32_t)(i + 1 - (1 << r));
-      cp_async<(int)sizeof(Tw)>(dst + i, tw + idx);
+      const int e = i + 1 - (1 << r);  // entry within the slice
+      const uint32_t idx = (1u << (logn - kWLog + r)) + (t << r) + (uint32_t)e;
+      const int pos = (r & 1) ? ((e & 1) << (r - 1)) + (e >> 1) : e;
+      cp_async<(int)sizeof(Tw)>(dst + (1 << r) - 1 + pos, tw + idx);
     }
   }
 }
@@ -134,7 +140,8 @@ __device__ __forceinline__ void w_geo(int th, int& pbase, int& blk) {
 }
 
 // One forward pass: CT stage 2P pairs (u, u+2) with slice 2P's entry blk,
-// stage 2P+1 pairs (u, u+1) with slice 2P+1's entries 2 blk + u/2.  Pass 0
+// stage 2P+1 pairs (u, u+1) with slice 2P+1's entries 2 blk + u/2 (staged at
+// positions blk and 2^(2P) + blk).  Pass 0
 // takes its words from the caller (registers); later passes read their
 // layout from shared memory.  With two operands (TWO) both share the
 // twiddles.  `trunc` omits the transform's last stage (Algorithm 8).
@@ -158,8 +165,8 @@ __device__ __forceinline__ void w_fwd_pass(W (&va)[4], W (&vb)[4], W* sa, W* sb,
     ct_bfly(vb[1], vb[3], t0.w, t0.wp, q, two_q);
   }
   if (!(P == kWPasses - 1 && trunc)) {
-    const Tw* t1 = tws + (1 << (2 * P + 1)) - 1 + 2 * blk;
-    const Tw t1a = t1[0], t1b = t1[1];
+    const Tw* t1 = tws + (1 << (2 * P + 1)) - 1 + blk;  // odd slice: evens, then odds
+    const Tw t1a = t1[0], t1b = t1[1 << (2 * P)];
     ct_bfly(va[0], va[1], t1a.w, t1a.wp, q, two_q);
     ct_bfly(va[2], va[3], t1b.w, t1b.wp, q, two_q);
     if constexpr (TWO) {
@@ -201,8 +208,8 @@ __device__ __forceinline__ void w_inv_pass(W (&v)[4], W* s, const typename WordT
   w_geo<W, E>(th, pb, blk);
   if constexpr (PI > 0) lat_ld<W, E>(v, s, pb);
   if (!(PI == 0 && trunc)) {
-    const Tw* t0 = tws + (1 << (2 * PF + 1)) - 1 + 2 * blk;
-    const Tw t0a = t0[0], t0b = t0[1];
+    const Tw* t0 = tws + (1 << (2 * PF + 1)) - 1 + blk;  // odd slice: evens, then odds
+    const Tw t0a = t0[0], t0b = t0[1 << (2 * PF)];
     gs_bfly_mode<HALVE>(v[0], v[1], t0a.w, t0a.wp, q, two_q, hq);
     gs_bfly_mode<HALVE>(v[2], v[3], t0b.w, t0b.wp, q, two_q, hq);
   }
