@@ -256,7 +256,8 @@ pm_status pm_polymul_uneven(pm_queue *q, const pm_job *jobs, uint32_t njobs, voi
 /* How pm_polymul_uneven runs the jobs with N >= 4096:
  *   PM_UNEVEN_PERSISTENT: one persistent work-queue launch (above);
  *   PM_UNEVEN_GROUPED: the units grouped by N, each group through the column
- *     and row kernels of pm_polymul (up to three launches per distinct N,
+ *     and row kernels of pm_polymul (rows of 1024 words for N >= 2^13, whole
+ *     4096-word rows for N = 2^12; up to three launches per distinct N,
  *     every unit's pointers and tables from a descriptor table) -- no
  *     dependency waits, the throughput kernels;
  *   PM_UNEVEN_AUTO (default): GROUPED when the batch has at least 8 rows of

@@ -1143,7 +1143,9 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       P.logn = (uint32_t)L;
       P.halving = (uint32_t)halving;
       P.fused = (uint32_t)fused;
-      P.row_ops = 2;
+      // N >= 2^13: the 1024-word split (measured faster at every batch
+      // size); N = 2^12: whole 4096-word rows with the two-operand kernel
+      P.row_ops = L >= 13 ? 4 : 2;
       if ((e = pm::launch_polymul_grouped(P, st)) != cudaSuccess)
         return cuda_fail(e, "grouped uneven launch");
       first += count[L];

@@ -106,6 +106,9 @@ cudaError_t wide_prepare();
 cudaError_t launch_polymul_wide(const KParams& P, cudaStream_t st, const PhaseEvents* pe);
 cudaError_t launch_ntt_fwd_wide(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_inv_wide(const KParams& P, cudaStream_t st);
+// Grouped uneven products of one N >= 2^13 (64-bit words, P.desc) through
+// the 1024-word split.
+cudaError_t launch_polymul_wide_grouped(const KParams& P, cudaStream_t st);
 cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st, int num_sms);
 
 // True when the polymul path for this N needs the [nunits][N] scratch.

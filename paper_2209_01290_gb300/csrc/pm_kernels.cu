@@ -856,6 +856,7 @@ static cudaError_t polymul_desc_r(const KParams& P, cudaStream_t st) {
 cudaError_t launch_polymul_grouped(const KParams& P, cudaStream_t st) {
   if (P.nunits == 0) return cudaSuccess;
   if (P.word32 || !P.desc) return cudaErrorInvalidValue;
+  if (P.row_ops == 4 && P.logn >= 13) return launch_polymul_wide_grouped(P, st);
   switch (P.logn) {
     case 12: return polymul_desc_r<1>(P, st);
     case 13: return polymul_desc_r<2>(P, st);

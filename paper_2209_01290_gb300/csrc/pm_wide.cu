@@ -254,11 +254,49 @@ __device__ __forceinline__ void w_inv(W (&v)[4], W* g_dst, bool final, W* s,
 
 // ------------------------------------------------------------- kernels
 
+// One unit's rows, tables and constants: from the batch layout [unit][N]
+// and the unit's limb, or, in grouped uneven launches (DESC, 64-bit words),
+// from the unit's descriptor.
+template <typename W, bool DESC>
+struct WUnit {
+  const W* a;
+  const W* b;
+  W* c;
+  W* s;
+  const typename WordT<W>::Tw* twf;
+  const typename WordT<W>::Tw* twi;
+  typename WordT<W>::LC K;
+  __device__ __forceinline__ WUnit(const KParams& P, uint32_t unit) {
+    if constexpr (DESC) {
+      static_assert(sizeof(W) == 8, "grouped launches take 64-bit words");
+      const UnitDesc& D = P.desc[unit];
+      a = D.a;
+      b = D.b;
+      c = D.c;
+      s = D.s;
+      twf = D.twf;
+      twi = D.twi;
+      K = ld_limb(D.lc);
+    } else {
+      const KView<W> V(P);
+      const uint32_t limb = unit % P.nlimbs;
+      const size_t base = (size_t)unit << P.logn;
+      a = V.a ? V.a + base : nullptr;
+      b = V.b ? V.b + base : nullptr;
+      c = V.c + base;
+      s = V.s ? V.s + base : nullptr;
+      twf = V.twf + ((size_t)limb << P.logn);
+      twi = V.twi + ((size_t)limb << P.logn);
+      K = ld_limb(V.lc + limb);
+    }
+  }
+};
+
 // In-row stages for n >= 10, one CTA per 1024-word row.  Polymul reads the
 // column images of a and b from c and s (n > 10) or a and b themselves
 // (n = 10); forward NTT rows read c in natural order and write it
 // bit-reversed and canonical; inverse NTT rows read c bit-reversed.
-template <int MODE, bool HALVE, typename W>
+template <int MODE, bool HALVE, typename W, bool DESC = false>
 __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   using Tw = typename WordT<W>::Tw;
   extern __shared__ __align__(16) uint64_t smem_raw[];
@@ -266,17 +304,16 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   Tw* tw_i = tw_f + kWTw;
   W* sa = reinterpret_cast<W*>(tw_i + kWTw);
   W* sb = sa + kWRowPad<W>;
-  const KView<W> V(P);
   const uint32_t logn = P.logn;
   const uint32_t cl = logn - kWLog;
   const uint32_t unit = blockIdx.x >> cl;
   const uint32_t t = blockIdx.x & ((1u << cl) - 1);
   if (unit >= P.nunits) return;  // whole CTA exits together
-  const uint32_t limb = unit % P.nlimbs;
-  const auto K = ld_limb(V.lc + limb);
-  const Tw* twf = V.twf + ((size_t)limb << logn);
-  const Tw* twi = V.twi + ((size_t)limb << logn);
-  const size_t off = ((size_t)unit << logn) + (size_t)t * kW;
+  const WUnit<W, DESC> U(P, unit);
+  const auto& K = U.K;
+  const Tw* twf = U.twf;
+  const Tw* twi = U.twi;
+  const size_t off = (size_t)t * kW;
   const bool single = (cl == 0);
   const int th = threadIdx.x;
   constexpr bool kFused = (MODE == MODE_POLYMUL_FUSED);
@@ -288,13 +325,13 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   if constexpr (MODE == MODE_INV) {
     // bit-reversed input in the last forward layout: words 4 th .. 4 th + 3
 #pragma unroll
-    for (int u = 0; u < 4; u++) va[u] = __ldcs(V.c + off + 4 * th + u);
+    for (int u = 0; u < 4; u++) va[u] = __ldcs(U.c + off + 4 * th + u);
   } else if constexpr (MODE == MODE_FWD) {
 #pragma unroll
-    for (int u = 0; u < 4; u++) va[u] = __ldcs(V.c + off + th + kWThreads * u);
+    for (int u = 0; u < 4; u++) va[u] = __ldcs(U.c + off + th + kWThreads * u);
   } else {
-    const W* ga = (single ? V.a : V.c) + off;
-    const W* gb = (single ? V.b : V.s) + off;
+    const W* ga = (single ? U.a : U.c) + off;
+    const W* gb = (single ? U.b : U.s) + off;
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       va[u] = __ldcs(ga + th + kWThreads * u);
@@ -307,11 +344,11 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   cp_async_wait_all();
   __syncthreads();
   if constexpr (MODE == MODE_INV) {
-    w_inv<HALVE>(va, V.c + off, single, sa, tw_i, th, K, false);
+    w_inv<HALVE>(va, U.c + off, single, sa, tw_i, th, K, false);
   } else if constexpr (MODE == MODE_FWD) {
     w_fwd<false>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, false);
 #pragma unroll
-    for (int u = 0; u < 4; u++) __stcs(V.c + off + 4 * th + u, reduce4(va[u], K.q, K.two_q));
+    for (int u = 0; u < 4; u++) __stcs(U.c + off + 4 * th + u, reduce4(va[u], K.q, K.two_q));
   } else {
     w_fwd<true>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, kFused);
     if constexpr (kFused) {
@@ -322,7 +359,7 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
       for (int u = 0; u < 4; u++)
         va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
     }
-    w_inv<HALVE>(va, V.c + off, single, sa, tw_i, th, K, kFused);
+    w_inv<HALVE>(va, U.c + off, single, sa, tw_i, th, K, kFused);
   }
 }
 
@@ -389,23 +426,22 @@ __device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw*
 // (a) goes to c, operand 1 (b) to the scratch s.  Every word of a column is
 // read (before the barrier) and written (after it) by the CTA that owns the
 // column, so c may alias a.
-template <int CL, typename W>
+template <int CL, typename W, bool DESC = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) {
   using S = WCol<CL>;
-  const KView<W> V(P);
-  const uint32_t logn = P.logn;
   const uint32_t tile = blockIdx.x % S::kTiles;
   const uint32_t rest = blockIdx.x / S::kTiles;
   const uint32_t op = rest % (uint32_t)nops, unit = rest / (uint32_t)nops;
   if (unit >= P.nunits) return;
+  const WUnit<W, DESC> U(P, unit);
+  if (DESC && op == 1 && U.a == U.b) return;  // a square: one image, read twice
   const int th = threadIdx.x;
   const int c = th % S::CT, j = th / S::CT;
-  const uint32_t limb = unit % P.nlimbs;
-  const auto K = ld_limb(V.lc + limb);
-  const auto* twf = V.twf + ((size_t)limb << logn);
-  const size_t base = ((size_t)unit << logn) + tile * S::CT + c;
-  const W* src = (op == 0 ? V.a : V.b) + base;
-  W* dst = (op == 0 ? V.c : V.s) + base;
+  const auto& K = U.K;
+  const auto* twf = U.twf;
+  const size_t base = tile * S::CT + c;
+  const W* src = (op == 0 ? U.a : U.b) + base;
+  W* dst = (op == 0 ? U.c : U.s) + base;
   W x[S::M];
 #pragma unroll
   for (int k = 0; k < S::M; k++) x[k] = __ldcs(src + (size_t)(j + S::J * k) * kW);
@@ -428,20 +464,18 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) 
 
 // Inverse column stages and the reduction, in place on c: the rows' lazy
 // output [0, 2q) in, canonical words out.
-template <int CL, bool HALVE, typename W>
+template <int CL, bool HALVE, typename W, bool DESC = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   using S = WCol<CL>;
-  const KView<W> V(P);
-  const uint32_t logn = P.logn;
   const uint32_t tile = blockIdx.x % S::kTiles;
   const uint32_t unit = blockIdx.x / S::kTiles;
   if (unit >= P.nunits) return;
+  const WUnit<W, DESC> U(P, unit);
   const int th = threadIdx.x;
   const int c = th % S::CT, j = th / S::CT;
-  const uint32_t limb = unit % P.nlimbs;
-  const auto K = ld_limb(V.lc + limb);
-  const auto* twi = V.twi + ((size_t)limb << logn);
-  W* p = V.c + ((size_t)unit << logn) + tile * S::CT + c;
+  const auto& K = U.K;
+  const auto* twi = U.twi;
+  W* p = U.c + tile * S::CT + c;
   W x[S::M];
   if constexpr (S::J > 1) {
 #pragma unroll
@@ -740,6 +774,33 @@ cudaError_t prepare_clu() {
   return cudaSuccess;
 }
 
+// Grouped uneven launch (64-bit words): the units of one N >= 2^13 through
+// the three wide-split kernels, each unit's rows, scratch, tables and
+// constants (the fused ones for an Algorithm 8 plan) from P.desc.
+template <int CL, bool H, bool F>
+cudaError_t wide_desc_cl(const KParams& P, cudaStream_t st) {
+  using W = uint64_t;
+  constexpr int MODE = F ? MODE_POLYMUL_FUSED : MODE_POLYMUL;
+  const size_t cols = (size_t)P.nunits * 2 * WCol<CL>::kTiles;
+  const size_t rows = (size_t)P.nunits << CL;
+  const size_t inv = (size_t)P.nunits * WCol<CL>::kTiles;
+  if (cols > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
+  k_wcol_fwd<CL, W, true><<<(unsigned)cols, kWColThreads, 0, st>>>(P, 2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_wrows<MODE, H, W, true><<<(unsigned)rows, kWThreads, kWRowsSmem<W>, st>>>(P);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_wcol_inv<CL, H, W, true><<<(unsigned)inv, kWColThreads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int CL>
+cudaError_t wide_desc(const KParams& P, cudaStream_t st) {
+  if (P.halving)
+    return P.fused ? wide_desc_cl<CL, true, true>(P, st) : wide_desc_cl<CL, true, false>(P, st);
+  return P.fused ? wide_desc_cl<CL, false, true>(P, st) : wide_desc_cl<CL, false, false>(P, st);
+}
+
 template <bool H, typename W>
 cudaError_t wide_prepare_w() {
   cudaError_t e;
@@ -753,6 +814,15 @@ cudaError_t wide_prepare_w() {
     if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kWRowsSmem<W>)) != cudaSuccess)
       return e;
+  }
+  if constexpr (sizeof(W) == 8) {  // the grouped (descriptor) rows exist for 64-bit words only
+    const void* desc_fns[] = {(const void*)k_wrows<MODE_POLYMUL, H, W, true>,
+                              (const void*)k_wrows<MODE_POLYMUL_FUSED, H, W, true>};
+    for (const void* f : desc_fns) {
+      if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kWRowsSmem<W>)) != cudaSuccess)
+        return e;
+    }
   }
   return cudaSuccess;
 }
@@ -777,6 +847,19 @@ cudaError_t launch_polymul_wide(const KParams& P, cudaStream_t st, const PhaseEv
 
 cudaError_t launch_ntt_fwd_wide(const KParams& P, cudaStream_t st) {
   return P.word32 ? ntt_fwd_wide_w<uint32_t>(P, st) : ntt_fwd_wide_w<uint64_t>(P, st);
+}
+
+cudaError_t launch_polymul_wide_grouped(const KParams& P, cudaStream_t st) {
+  if (P.nunits == 0) return cudaSuccess;
+  if (P.word32 || !P.desc) return cudaErrorInvalidValue;
+  switch (P.logn) {
+    case 13: return wide_desc<3>(P, st);
+    case 14: return wide_desc<4>(P, st);
+    case 15: return wide_desc<5>(P, st);
+    case 16: return wide_desc<6>(P, st);
+    case 17: return wide_desc<7>(P, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_ntt_inv_wide(const KParams& P, cudaStream_t st) {
