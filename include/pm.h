@@ -337,10 +337,11 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  *   3 = 1024 threads per row in radix-4 passes (1 CTA per SM);
  *   4 = the transform as N/1024 rows of 1024 words (N >= 1024): 256
  *       threads per row in radix-4 passes with the row's twiddles staged in
- *       shared memory, up to 4 CTAs per SM; for N = 2^11 .. 2^13 one launch
- *       (a thread-block cluster of N/1024 CTAs per unit exchanging the
- *       column stages through distributed shared memory, no scratch), from
- *       2^14 three launches (column stages, rows, column stages);
+ *       shared memory, up to 4 CTAs per SM; for N = 2^11 .. 2^13, and N =
+ *       2^14 batches of up to 16 units where the device runs clusters of 16
+ *       CTAs, one launch (a thread-block cluster of N/1024 CTAs per unit
+ *       exchanging the column stages through distributed shared memory),
+ *       otherwise three launches (column stages, rows, column stages);
  *   0 = by N, word size and batch size (measured on GB300): 4 for 64-bit
  *       words, except N = 2^12 batches above 64 units; 4 for 32-bit words
  *       in batches of up to 2^20 words; otherwise 3 while the batch has at

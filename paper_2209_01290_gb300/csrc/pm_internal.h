@@ -96,10 +96,10 @@ cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st);
 cudaError_t launch_ntt_inv(const KParams& P, cudaStream_t st);
 cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms);
 
-// The latency split (pm_wide.cu): rows of 1024 words, chosen with row_ops 4,
-// for N = 2^10 .. 2^17: one launch up to N = 2^13 (a thread-block cluster
-// per unit above 2^10, no scratch), three from 2^14 (the [nunits][N] scratch
-// of the 4096-word split).
+// The 1024-word split (pm_wide.cu), chosen with row_ops 4, for N = 2^10 ..
+// 2^17: one launch up to N = 2^13 and for small N = 2^14 batches (a
+// thread-block cluster per unit above 2^10, no scratch), otherwise three
+// (the [nunits][N] scratch of the 4096-word split).
 bool wide_polymul_ok(uint32_t logn);
 bool wide_ntt_ok(uint32_t logn);
 cudaError_t wide_prepare();

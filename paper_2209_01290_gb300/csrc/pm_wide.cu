@@ -33,7 +33,9 @@
 //                    after another.
 //   k_wcol_inv<CL> : the CL inverse column stages (k_wcol_fwd mirrored), the
 //                    1/N fold in the last stage and the reduction to [0, q).
-//   k_wclu<CL>     : n = 11..13 (CL = 1..3) in one launch, one thread-block
+//   k_wclu<CL>     : n = 11..13 (CL = 1..3; and n = 14 in batches of up to
+//                    16 units, with clusters of 16 where the device allows
+//                    that non-portable size) in one launch, one thread-block
 //                    cluster of 2^CL CTAs per unit (CTA rank t = row t).
 //                    Each CTA runs the column stages of 1024/2^CL columns
 //                    and writes row t' of every column into CTA t''s shared
@@ -685,12 +687,23 @@ cudaError_t clu(const KParams& P, cudaStream_t st) {
     case 1: return P.halving ? clu_cl<MODE, true, W, 1>(P, st) : clu_cl<MODE, false, W, 1>(P, st);
     case 2: return P.halving ? clu_cl<MODE, true, W, 2>(P, st) : clu_cl<MODE, false, W, 2>(P, st);
     case 3: return P.halving ? clu_cl<MODE, true, W, 3>(P, st) : clu_cl<MODE, false, W, 3>(P, st);
+    case 4: return P.halving ? clu_cl<MODE, true, W, 4>(P, st) : clu_cl<MODE, false, W, 4>(P, st);
   }
   return cudaErrorInvalidValue;
 }
 
-// Units of N = 2^11 .. 2^13 run as one cluster launch.
-inline bool clustered(uint32_t logn) { return logn > kWLog && logn <= kWLog + 3; }
+// N = 2^14 as one launch needs clusters of 16 CTAs (above the portable 8):
+// used when the device schedules them (checked when the kernels are
+// prepared) and for batches of at most kClu14MaxUnits units.
+bool g_clu16 = false;
+constexpr uint32_t kClu14MaxUnits = 16;  // measured: faster up to 16 units, slower from 64
+
+// Units of N = 2^11 .. 2^13 (and small batches of 2^14) run as one cluster
+// launch.
+inline bool clustered(uint32_t logn, uint32_t nunits) {
+  return (logn > kWLog && logn <= kWLog + 3) ||
+         (logn == kWLog + 4 && g_clu16 && nunits <= kClu14MaxUnits);
+}
 
 inline cudaError_t mark(const PhaseEvents* pe, int k, cudaStream_t st) {
   return (pe && k < pe->n) ? cudaEventRecord(pe->ev[k], st) : cudaSuccess;
@@ -709,7 +722,7 @@ cudaError_t polymul_wide_w(const KParams& P0, cudaStream_t st, const PhaseEvents
   };
   cudaError_t e = mark(pe, 0, st);
   if (e != cudaSuccess) return e;
-  if (P.logn == kWLog || clustered(P.logn)) {
+  if (P.logn == kWLog || clustered(P.logn, P.nunits)) {
     if (P.logn == kWLog)
       e = prows(P);
     else
@@ -741,7 +754,7 @@ cudaError_t polymul_wide_w(const KParams& P0, cudaStream_t st, const PhaseEvents
 template <typename W>
 cudaError_t ntt_fwd_wide_w(const KParams& P0, cudaStream_t st) {
   if (P0.nunits == 0) return cudaSuccess;
-  if (clustered(P0.logn)) return clu<MODE_FWD, W>(P0, st);
+  if (clustered(P0.logn, P0.nunits)) return clu<MODE_FWD, W>(P0, st);
   KParams P = P0;
   if (P.logn > kWLog) {
     P.a = P.c;  // in place: the column stages read and write x
@@ -754,7 +767,7 @@ cudaError_t ntt_fwd_wide_w(const KParams& P0, cudaStream_t st) {
 template <typename W>
 cudaError_t ntt_inv_wide_w(const KParams& P, cudaStream_t st) {
   if (P.nunits == 0) return cudaSuccess;
-  if (clustered(P.logn)) return clu<MODE_INV, W>(P, st);
+  if (clustered(P.logn, P.nunits)) return clu<MODE_INV, W>(P, st);
   cudaError_t e = wrows<MODE_INV, W>(P, st);
   if (e != cudaSuccess || P.logn == kWLog) return e;
   return wcol_inv<W>(P, st);
@@ -801,12 +814,49 @@ cudaError_t wide_desc(const KParams& P, cudaStream_t st) {
   return P.fused ? wide_desc_cl<CL, false, true>(P, st) : wide_desc_cl<CL, false, false>(P, st);
 }
 
+// Clusters of 16 CTAs for N = 2^14: allowed (non-portable size) and
+// schedulable on this device?  A refusal only leaves g_clu16 false.
 template <bool H, typename W>
-cudaError_t wide_prepare_w() {
+bool prepare_clu16() {
+  const void* fns[] = {(const void*)k_wclu<MODE_POLYMUL, H, W, 4>,
+                       (const void*)k_wclu<MODE_POLYMUL_FUSED, H, W, 4>,
+                       (const void*)k_wclu<MODE_FWD, H, W, 4>,
+                       (const void*)k_wclu<MODE_INV, H, W, 4>};
+  for (const void* f : fns) {
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWRowsSmem<W>) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(kWThreads, 1, 1);
+    cfg.dynamicSmemBytes = kWRowsSmem<W>;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return true;
+}
+
+template <bool H, typename W>
+cudaError_t wide_prepare_w(bool& clu16) {
   cudaError_t e;
   if ((e = prepare_clu<H, W, 1>()) != cudaSuccess || (e = prepare_clu<H, W, 2>()) != cudaSuccess ||
       (e = prepare_clu<H, W, 3>()) != cudaSuccess)
     return e;
+  clu16 = clu16 && prepare_clu16<H, W>();
   const void* fns[] = {(const void*)k_wrows<MODE_POLYMUL, H, W>,
                        (const void*)k_wrows<MODE_POLYMUL_FUSED, H, W>,
                        (const void*)k_wrows<MODE_FWD, H, W>, (const void*)k_wrows<MODE_INV, H, W>};
@@ -835,10 +885,14 @@ bool wide_ntt_ok(uint32_t logn) { return logn >= kWLog && logn <= 17; }
 
 cudaError_t wide_prepare() {
   cudaError_t e;
-  if ((e = wide_prepare_w<false, uint64_t>()) != cudaSuccess) return e;
-  if ((e = wide_prepare_w<true, uint64_t>()) != cudaSuccess) return e;
-  if ((e = wide_prepare_w<false, uint32_t>()) != cudaSuccess) return e;
-  return wide_prepare_w<true, uint32_t>();
+  bool clu16 = true;
+  if ((e = wide_prepare_w<false, uint64_t>(clu16)) != cudaSuccess ||
+      (e = wide_prepare_w<true, uint64_t>(clu16)) != cudaSuccess ||
+      (e = wide_prepare_w<false, uint32_t>(clu16)) != cudaSuccess ||
+      (e = wide_prepare_w<true, uint32_t>(clu16)) != cudaSuccess)
+    return e;
+  g_clu16 = clu16;
+  return cudaSuccess;
 }
 
 cudaError_t launch_polymul_wide(const KParams& P, cudaStream_t st, const PhaseEvents* pe) {
