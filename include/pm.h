@@ -88,7 +88,9 @@ pm_status pm_find_params(uint32_t log2n, uint32_t nlimbs, uint32_t qbits,
  * The plan builds, per limb, Psi_br[i] = psi^br(i) and
  * Psi^-1_br[i] = psi^-br(i) with their Shoup companions floor(w 2^64 / q),
  * mu = floor(2^(2m+1)/q) of Algorithm 4, and N^-1 for the inverse scaling.
- * Device memory: 32 N + 128 bytes per limb.  Synchronous.
+ * Device memory: 32 N + 128 bytes per limb (PM_PLAN_FUSED: 32 N + 256;
+ * PM_PLAN_WORD32: 16 N + 64, or 16 N + 128 with PM_PLAN_FUSED).
+ * Synchronous.
  * Errors: PM_ERR_N, PM_ERR_Q, PM_ERR_PSI, PM_ERR_OOM, PM_ERR_CUDA. */
 pm_status pm_plan_create(pm_plan **out, uint32_t log2n, uint32_t nlimbs,
                          const uint64_t *q, const uint64_t *psi, int device);
