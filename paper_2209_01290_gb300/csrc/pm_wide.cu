@@ -1,7 +1,9 @@
-// pm_wide.cu -- the latency split for small batches: one N = 2^n point
+// pm_wide.cu -- the default split for 64-bit words: one N = 2^n point
 // transform viewed as R = N/1024 rows of 1024 words (arxiv 2209.01290,
 // Algorithms 6 and 7; the same decomposition as pm_kernels.cu with a shorter
-// row).
+// row).  Measured faster than the 4096-word rows for single products and for
+// large batches alike (fewer in-row stages per unit, more warps per SM,
+// twiddles from shared memory).
 //
 // Why a second split.  With 4096-word rows one N = 2^16 product has 16 row
 // tasks and keeps 16 SMs busy; each row task (two forward and one inverse
@@ -143,9 +145,8 @@ __device__ __forceinline__ void w_geo(int th, int& pbase, int& blk) {
 
 // One forward pass: CT stage 2P pairs (u, u+2) with slice 2P's entry blk,
 // stage 2P+1 pairs (u, u+1) with slice 2P+1's entries 2 blk + u/2 (staged at
-// positions blk and 2^(2P) + blk).  Pass 0
-// takes its words from the caller (registers); later passes read their
-// layout from shared memory.  With two operands (TWO) both share the
+// positions blk and 2^(2P) + blk).  Pass 0 takes its words from the caller
+// (registers); later passes read their layout from shared memory.  With two operands (TWO) both share the
 // twiddles.  `trunc` omits the transform's last stage (Algorithm 8).
 template <int P, bool TWO, typename W>
 __device__ __forceinline__ void w_fwd_pass(W (&va)[4], W (&vb)[4], W* sa, W* sb,

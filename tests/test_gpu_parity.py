@@ -248,3 +248,30 @@ def test_streams_and_large_batch_sampled(torch_cuda, oracle):
     for _ in range(4):
         p, l, k = int(rng.integers(P)), int(rng.integers(L)), int(rng.integers(n))
         assert int(got[p, l, k]) == schoolbook_coeff(a[p, l], b[p, l], qs[l], k)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("row_ops", [0, 2], ids=["default", "rows4096"])
+def test_headline_batch_sampled(torch_cuda, oracle, row_ops):
+    """The benchmark's own workload and launch: 1024 products of N=2^16 with
+    the largest 60-bit prime in one pm_polymul (default tuning: the
+    1024-word split; also the 4096-word split).  Sampled units are checked in
+    full against the oracle, sampled coefficients against the definition,
+    and every output word is checked to be reduced."""
+    from paper_2209_01290_gb300 import inputs
+    log2n, P = 16, 1024
+    n = 1 << log2n
+    plan, qs, psis = _plan(log2n, 1, variant=(0, row_ops) if row_ops else None)
+    da = inputs.uniform_limbs_torch(inputs.seed_for(9), qs, P, n)
+    db = inputs.uniform_limbs_torch(inputs.seed_for(9) + 1, qs, P, n)
+    dc = plan.polymul(da, db)
+    torch_cuda.cuda.synchronize()
+    assert plan.check_reduced(dc)
+    rng = np.random.default_rng(16)
+    for p in [0, P - 1] + [int(x) for x in rng.choice(np.arange(1, P - 1), 2, replace=False)]:
+        a, b = to_host(da[p, 0]), to_host(db[p, 0])
+        assert np.array_equal(to_host(dc[p, 0]), oracle.polymul_ntt(a, b, qs[0], psis[0])), p
+    for _ in range(3):
+        p, k = int(rng.integers(P)), int(rng.integers(n))
+        got = int(to_host(dc[p, 0, k:k + 1])[0])
+        assert got == schoolbook_coeff(to_host(da[p, 0]), to_host(db[p, 0]), qs[0], k)
