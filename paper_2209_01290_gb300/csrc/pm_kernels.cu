@@ -24,7 +24,9 @@
 //                     product step (Algorithm 4, or Algorithm 8's pair step)
 //                     and the 12 inverse in-row stages; rows are exchanged
 //                     through padded shared memory between the radix-16
-//                     passes.  The default polymul row kernel.
+//                     passes.  The 4096-word row kernel for
+//                     N = 2^12 batches and large 32-bit batches (row_ops 2);
+//                     the 1024-word rows of pm_wide.cu serve the rest.
 //   k_rows<MODE>    : the same passes one operand at a time (forward or
 //                     inverse NTT rows, and polymul with row_ops 1).
 //   k_col_inv<R>    : the n-12 inverse column stages and the final reduction.
