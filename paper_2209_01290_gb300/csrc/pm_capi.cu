@@ -856,8 +856,9 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
   DeviceGuard g(plan->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  // candidates: the split path with either row kernel, the persistent launch
-  // with a few pipeline distances
+  // candidates: the split path with each row kernel (4096-word rows: the
+  // two-operand, one-operand and 1024-thread kernels; 1024-word rows), the
+  // persistent launch with a few pipeline distances
   std::vector<pm_tuning> cand;
   cand.push_back(pm_tuning{PM_VARIANT_SPLIT, 3, 8, 64, 2});
   if (plan->logn >= 12 && plan->logn != 13) {
