@@ -53,18 +53,6 @@ def rows_kernel_mulmods(log2n: int, row_log: int = 12) -> int:
     return 2 * rows_stages * (n // 2) + n + rows_stages * (n // 2)
 
 
-def auto_row_ops(log2n: int, units: int, sms: int, word32: bool = False) -> int:
-    """The library's row kernel for row_ops 0 (pm.h): rows of 1024 words
-    (4) for 64-bit words except N = 2^12 batches above 64 units, and for
-    32-bit words in batches of up to 2^20 words; otherwise 4096-word rows
-    (3 up to one row per SM, else 2)."""
-    wide = log2n >= 10 and ((units << log2n) <= (1 << 20) if word32
-                            else not (log2n == 12 and units > 64))
-    if wide:
-        return 4
-    return 3 if (units << max(log2n - 12, 0)) <= sms else 2
-
-
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons; only samples
     taken inside the timed window (wall clock) are summarised."""
@@ -318,10 +306,8 @@ def run_gpu(args):
         dom_mulmods = mulmods_per_polymul(log2n) * units
     elif log2n >= 14:
         dom_idx = 1
-        row_ops = tuning.row_ops
-        if row_ops == 0:  # the library's choice by N and batch size
-            sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            row_ops = auto_row_ops(log2n, units, sms)
+        # the row kernel the library picks for this batch (row_ops 0 resolved)
+        row_ops = capi.pm_plan_resolve_tuning(plan.handle, npoly).row_ops
         dom_name = {2: "k_rows2<POLYMUL> (in-row stages of a and b together, Barrett pointwise, "
                        "inverse in-row stages)",
                     3: "k_rows_lat<POLYMUL> (1024 threads per row, radix-4 passes)",

@@ -373,6 +373,12 @@ pm_status pm_plan_autotune(pm_plan *plan, uint32_t npoly, void *stream, pm_tunin
 pm_status pm_plan_tune(pm_plan *plan, const pm_tuning *t);
 pm_status pm_plan_get_tuning(const pm_plan *plan, pm_tuning *t);
 
+/* The launch choice a pm_polymul (or pm_ntt_fwd / pm_ntt_inv) of npoly
+ * polynomials on this plan makes: the plan's tuning with row_ops 0 replaced
+ * by the row kernel the rule above picks for that batch (1..4).  No device
+ * work.  PM_ERR_ARG for a NULL tuning or an invalid batch size. */
+pm_status pm_plan_resolve_tuning(const pm_plan *plan, uint32_t npoly, pm_tuning *t);
+
 /* Test hook: fault injection on the host side of the next persistent
  * polymul launch on this plan (kind 0 clears it).
  *   PM_FAULT_WITHHOLD_SIGNAL : the launch's row tasks wait for one more

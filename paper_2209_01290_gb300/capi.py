@@ -49,6 +49,7 @@ SIGNATURES = {
     "pm_plan_inject_fault": (_i32, [_vp, _i32]),
     "pm_plan_autotune": (_i32, [_vp, _u32, _vp, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]),
     "pm_plan_get_tuning": (_i32, [_vp, ctypes.c_void_p]),
+    "pm_plan_resolve_tuning": (_i32, [_vp, _u32, ctypes.c_void_p]),
     "pm_plan_set_phase_events": (_i32, [_vp, ctypes.POINTER(_vp), _i32]),
     "pm_last_error": (ctypes.c_char_p, []),
     "pm_last_error_string": (_i32, [ctypes.c_char_p, _sz]),
@@ -273,6 +274,13 @@ def pm_plan_inject_fault(plan: int, kind: int) -> None:
 def pm_plan_get_tuning(plan: int) -> PmTuning:
     t = PmTuning()
     _call("pm_plan_get_tuning", plan, ctypes.byref(t))
+    return t
+
+
+def pm_plan_resolve_tuning(plan: int, npoly: int) -> PmTuning:
+    """The launch choice for a batch of npoly polynomials (row_ops resolved)."""
+    t = PmTuning()
+    _call("pm_plan_resolve_tuning", plan, npoly, ctypes.byref(t))
     return t
 
 

@@ -935,6 +935,16 @@ pm_status pm_plan_get_tuning(const pm_plan* plan, pm_tuning* t) {
   return ok();
 }
 
+pm_status pm_plan_resolve_tuning(const pm_plan* plan, uint32_t npoly, pm_tuning* t) {
+  pm_status s = check_plan(plan);
+  if (s != PM_OK) return s;
+  if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
+  if ((s = check_batch(plan, npoly)) != PM_OK) return s;
+  *t = plan->tune;
+  t->row_ops = base_params(plan, npoly).row_ops;  // the same rule as the launch
+  return ok();
+}
+
 
 }  // extern "C"
 

@@ -1,7 +1,6 @@
 """Host-side accounting of bench.py (no GPU): the mulmods the roofline
 attributes to the row kernel plus those of the column kernels make up the
-whole product of Eq. 2, for both row lengths; the row-kernel rule mirrors
-the library's (pm.h, row_ops 0)."""
+whole product of Eq. 2, for both row lengths."""
 import os
 import sys
 
@@ -25,19 +24,3 @@ def test_mulmods_closed_form():
     assert bench.mulmods_per_polymul(16) == 25 * (1 << 16)
     assert bench.rows_kernel_mulmods(16, 10) == 16 * (1 << 16)
     assert bench.rows_kernel_mulmods(16, 12) == 19 * (1 << 16)
-
-
-def test_auto_row_ops_rule():
-    import bench
-    assert all(bench.auto_row_ops(n, u, 152) == 4 for n in (10, 11, 13, 14, 16, 17)
-               for u in (1, 64, 1024, 1 << 20))
-    assert bench.auto_row_ops(12, 64, 152) == 4
-    assert bench.auto_row_ops(12, 65, 152) == 3
-    assert bench.auto_row_ops(12, 152, 152) == 3
-    assert bench.auto_row_ops(12, 153, 152) == 2
-    assert bench.auto_row_ops(16, 16, 152, word32=True) == 4
-    assert bench.auto_row_ops(16, 17, 152, word32=True) == 2
-    assert bench.auto_row_ops(12, 256, 152, word32=True) == 4
-    assert bench.auto_row_ops(12, 257, 152, word32=True) == 2
-    assert bench.auto_row_ops(14, 64, 152, word32=True) == 4
-    assert bench.auto_row_ops(14, 65, 152, word32=True) == 2

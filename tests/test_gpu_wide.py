@@ -162,3 +162,30 @@ def test_wide_tuning_range():
     with pytest.raises(capi.PMError) as e:
         capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=5)
     assert e.value.status == -1
+
+
+def test_resolved_row_kernel_rule():
+    """pm_plan_resolve_tuning reports the rule pm.h states for row_ops 0:
+    1024-word rows for 64-bit words except N = 2^12 above 64 units (then
+    1024-thread rows up to one row per SM, two-operand rows above); 32-bit
+    words: 1024-word rows up to 2^20 words per batch.  A set row_ops is kept."""
+    import torch
+    from paper_2209_01290_gb300 import Plan, capi
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cases = [(12, 1, False), (12, 64, False), (12, 65, False), (12, sms, False),
+             (12, sms + 1, False), (16, 1, False), (16, 4096, False), (10, 4096, False),
+             (16, 16, True), (16, 17, True), (12, 256, True), (12, 257, True)]
+    for log2n, npoly, w32 in cases:
+        qs, psis = capi.pm_find_params(log2n, 1, 30 if w32 else 60)
+        plan = Plan(1 << log2n, qs, psis, word32=w32)
+        got = capi.pm_plan_resolve_tuning(plan.handle, npoly).row_ops
+        if (npoly << log2n) <= (1 << 20) if w32 else not (log2n == 12 and npoly > 64):
+            want = 4
+        else:
+            want = 3 if (npoly << max(log2n - 12, 0)) <= sms else 2
+        assert got == want, (log2n, npoly, w32, got)
+        assert capi.pm_plan_get_tuning(plan.handle).row_ops == 0
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=1)
+        assert capi.pm_plan_resolve_tuning(plan.handle, npoly).row_ops == 1
+    with pytest.raises(capi.PMError):
+        capi.pm_plan_resolve_tuning(plan.handle, 0)
