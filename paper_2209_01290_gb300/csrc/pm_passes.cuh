@@ -165,7 +165,9 @@ __device__ __forceinline__ void gs16(W (&v)[16], const typename WordT<W>::Tw* __
 
 // Merged CT on a column of R words (the first log2 R stages of the N-point
 // transform): stage s pairs (t, t + R >> (s+1)) with twiddle Psi_br[2^s + blk].
-template <int R, int S, typename W>
+// RED = false (wide lazy ranges, canonical input, R <= 128) reduces nothing:
+// the outputs stay below (1 + 2 log2 R) q <= 15q.
+template <int R, int S, bool RED, typename W>
 __device__ __forceinline__ void ct_col_stage(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
                                              W q, W two_q) {
   if constexpr ((1 << S) < R) {
@@ -182,31 +184,35 @@ __device__ __forceinline__ void ct_col_stage(W (&x)[R], const typename WordT<W>:
       for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
 #pragma unroll
         for (int u0 = 0; u0 < h; u0++)
-          ct_bfly(x[(blk + e) * 2 * h + u0], x[(blk + e) * 2 * h + u0 + h], t[e].w, t[e].wp, q,
-                  two_q);
+          ct_bfly_m<RED>(x[(blk + e) * 2 * h + u0], x[(blk + e) * 2 * h + u0 + h], t[e].w,
+                         t[e].wp, q, two_q, two_q);
     }
-    ct_col_stage<R, S + 1>(x, tw, q, two_q);
+    ct_col_stage<R, S + 1, RED>(x, tw, q, two_q);
   }
 }
 
-template <int R, typename W>
+template <int R, typename W, bool RED = true>
 __device__ __forceinline__ void ct_col(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
                                        W q, W two_q) {
-  ct_col_stage<R, 0>(x, tw, q, two_q);
+  ct_col_stage<R, 0, RED>(x, tw, q, two_q);
 }
 
 // Merged GS on a column of R words (the last log2 R stages): the GS stage
 // with k = 4096 * 2^E pairs (t, t + 2^E) with twiddle
 // Psi^-1_br[(R >> (E+1)) + (t >> (E+1))].  Without per-stage halving the
-// final stage (2^E = R/2, the transform's last) folds in 1/N.
-template <int R, int E, bool HALVE, typename W>
+// final stage (2^E = R/2, the transform's last) folds in 1/N.  LZ (wide
+// lazy ranges, never with halving): inputs below 8q, every sum reduced by
+// 8q, differences formed with + 8q.
+template <int R, int E, bool HALVE, bool LZ, typename W>
 __device__ __forceinline__ void gs_col_stage(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
                                              const typename WordT<W>::LC& K) {
+  static_assert(!(LZ && HALVE), "wide lazy ranges fold 1/N at the end");
   if constexpr ((1 << E) < R) {
     constexpr int h = 1 << E;
+    const W m = LZ ? W(K.two_q << 2) : K.two_q;
     if constexpr (!HALVE && 2 * h == R) {
 #pragma unroll
-      for (int u0 = 0; u0 < h; u0++) gs_bfly_last(x[u0], x[u0 + h], K);
+      for (int u0 = 0; u0 < h; u0++) gs_bfly_last_m(x[u0], x[u0 + h], K, m);
     } else {
       constexpr int nb = R / (2 * h);  // table index nb + blk, even when nb > 1
 #pragma unroll
@@ -219,19 +225,24 @@ __device__ __forceinline__ void gs_col_stage(W (&x)[R], const typename WordT<W>:
 #pragma unroll
         for (int e = 0; e < (nb > 1 ? 2 : 1); e++)
 #pragma unroll
-          for (int u0 = 0; u0 < h; u0++)
-            gs_bfly_mode<HALVE>(x[(blk + e) * 2 * h + u0], x[(blk + e) * 2 * h + u0 + h], t[e].w,
-                                t[e].wp, K.q, K.two_q, K.half_q1);
+          for (int u0 = 0; u0 < h; u0++) {
+            W& a = x[(blk + e) * 2 * h + u0];
+            W& b = x[(blk + e) * 2 * h + u0 + h];
+            if constexpr (LZ)
+              gs_bfly_m<true>(a, b, t[e].w, t[e].wp, K.q, m);
+            else
+              gs_bfly_mode<HALVE>(a, b, t[e].w, t[e].wp, K.q, K.two_q, K.half_q1);
+          }
       }
     }
-    gs_col_stage<R, E + 1, HALVE>(x, tw, K);
+    gs_col_stage<R, E + 1, HALVE, LZ>(x, tw, K);
   }
 }
 
-template <int R, bool HALVE, typename W>
+template <int R, bool HALVE, typename W, bool LZ = false>
 __device__ __forceinline__ void gs_col(W (&x)[R], const typename WordT<W>::Tw* __restrict__ tw,
                                        const typename WordT<W>::LC& K) {
-  gs_col_stage<R, 0, HALVE>(x, tw, K);
+  gs_col_stage<R, 0, HALVE, LZ>(x, tw, K);
 }
 
 __device__ __forceinline__ LimbConst ld_limb(const LimbConst* __restrict__ p) {
