@@ -183,12 +183,13 @@ def run_reference(args):
     rank, ws, local, dist = _dist()
     if rank != 0:
         return 0
-    from paper_2209_01290_gb300 import capi
-    qs, psis = capi.pm_find_params(args.log2n, args.limbs, 60)
+    # the oracle's own parameter search: this arm maps no GPU library
     import oracle
     from paper_2209_01290_gb300 import inputs
-    cores = os.cpu_count() or 1
     n = 1 << args.log2n
+    qs = oracle.find_primes(n, args.limbs, 60)
+    psis = [oracle.find_psi(q, n) for q in qs]
+    cores = os.cpu_count() or 1
     per_step = cores  # one product per core per step
     a, b = inputs.operand_pair(inputs.seed_for(1), qs, max(1, per_step // args.limbs), n)
     A, B = a.reshape(-1, n)[:per_step], b.reshape(-1, n)[:per_step]
@@ -730,7 +731,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--log2n", type=int, default=16)
     ap.add_argument("--limbs", type=int, default=1)
-    ap.add_argument("--batch", type=int, default=1024, help="products per step")
+    ap.add_argument("--batch", type=int, default=4096,
+                    help="products per step (default: 4096 products of N=2^16, 6 GiB of "
+                         "operands and result per step)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="default", choices=["default", "split", "persistent"])

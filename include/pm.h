@@ -164,10 +164,15 @@ pm_status pm_ntt_inv(const pm_plan *plan, uint64_t *d_x, uint32_t npoly, void *s
 pm_status pm_pointwise(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
                        uint64_t *d_c, uint32_t npoly, void *stream);
 
-/* Negacyclic product of every unit, fused in one launch (Eq. 2): forward
- * NTT of a and b, pointwise product, inverse NTT with 1/N folded in.
- * d_a, d_b, d_c: device [npoly][nlimbs][N].  d_c may alias d_a or d_b
- * (each unit reads all of its inputs before it writes any output). */
+/* Negacyclic product of every unit (Eq. 2): forward NTT of a and b,
+ * pointwise product, inverse NTT with 1/N folded in.  N <= 2^13 (and small
+ * batches at N = 2^14) run as one launch; larger N run as three launches on
+ * `stream` (the forward column stages of a and b, one kernel that fuses the
+ * in-row forward stages, the pointwise product and the in-row inverse
+ * stages, then the inverse column stages), or as one persistent launch when
+ * pm_plan_tune selects it.  d_a, d_b, d_c: device [npoly][nlimbs][N].  d_c
+ * may alias d_a or d_b (each unit reads all of its inputs before it writes
+ * any output). */
 pm_status pm_polymul(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
                      uint64_t *d_c, uint32_t npoly, void *stream);
 
@@ -189,17 +194,23 @@ pm_status pm_check_reduced32(const pm_plan *plan, const uint32_t *d_x, uint32_t 
  * memory: code running while another memory manager owns the device pool,
  * or latency-critical paths that cannot take the device-wide synchronisation
  * of cudaFree.  The paper has no counterpart; this is a deployment variant.
- * The caller still provides a, b and c.  For N >= 2^14 the products need
- * scratch: it is a fixed 16 MiB array inside the library (2^21 words, held
- * on every device that loads the library until the process exits), so the
- * batch must satisfy npoly * nlimbs * N <= 2^21; larger batches are
- * rejected with PM_ERR_ARG.  No cudaMalloc/cudaFree or other allocating
- * call is made.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) once; make that first call before any
- * stream capture.  All calls share the one array and the scratch needs no
- * clearing (every word is written before it is read within a call), so calls
- * that overlap on the GPU -- on different streams or from several threads --
- * race on it: issue them on one stream.  N < 2^14 uses no scratch. */
+ * The caller still provides a, b and c.  Products of two distinct operands
+ * at N >= 2^14 that run as three launches need scratch for b's column
+ * image: it is a fixed 16 MiB array inside the library (2^21 words, held on
+ * every device that loads the library until the process exits), so such a
+ * batch must satisfy npoly * nlimbs * N <= 2^21; larger ones are rejected
+ * with PM_ERR_ARG.  Squares (d_a == d_b), N < 2^14 and the one-launch
+ * cluster batches use no scratch and have no such limit.  No cudaMalloc,
+ * cudaFree or other allocating call is made.  The first call on a device
+ * that needs the scratch looks up the array's device address
+ * (cudaGetSymbolAddress) once and caches it per device ordinal; make that
+ * first call before any stream capture, and do not rely on the cache across
+ * cudaDeviceReset (the address belongs to the context that looked it up).
+ * The launch choice is the plan's split path (a persistent tuning is not
+ * used).  All calls share the one array and the scratch needs no clearing
+ * (every word is written before it is read within a call), so calls that
+ * overlap on the GPU -- on different streams or from several threads --
+ * race on it: issue them on one stream. */
 pm_status pm_polymul_noalloc(const pm_plan *plan, const uint64_t *d_a, const uint64_t *d_b,
                              uint64_t *d_c, uint32_t npoly, void *stream);
 

@@ -595,13 +595,19 @@ pm_status pm_polymul_noalloc(const pm_plan* plan, const uint64_t* d_a, const uin
   if (!d_a || !d_b || !d_c || !aligned16(d_a) || !aligned16(d_b) || !aligned16(d_c))
     return fail(PM_ERR_ARG, "NULL or misaligned pointer");
   if ((s = check_batch(plan, npoly)) != PM_OK) return s;
-  pm::KParams P = base_params(plan, npoly);
+  pm::KParams P;
+  {
+    // the launch choice (plan->tune) is read under the plan's lock, since
+    // pm_plan_tune / pm_plan_autotune may rewrite it from another thread
+    std::lock_guard<std::mutex> lk(const_cast<pm_plan*>(plan)->mu);
+    P = base_params(plan, npoly);
+  }
   P.a = d_a;
   P.b = d_b;
   P.c = d_c;
   DeviceGuard g(plan->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  if (pm::polymul_needs_scratch(plan->logn)) {
+  if (pm::polymul_writes_scratch(P)) {
     const uint64_t words = (uint64_t)P.nunits << plan->logn;
     if (words > kNoAllocScratchWords)
       return fail(PM_ERR_ARG,

@@ -101,6 +101,9 @@ cudaError_t launch_pointwise(const KParams& P, cudaStream_t st, int num_sms);
 // thread-block cluster per unit above 2^10, no scratch), otherwise three
 // (the [nunits][N] scratch of the 4096-word split).
 bool wide_polymul_ok(uint32_t logn);
+// True when the 1024-word split runs this polymul batch as one launch
+// (N = 2^10, or the cluster kernel), which uses no scratch.
+bool wide_single_launch(uint32_t logn, uint32_t nunits);
 bool wide_ntt_ok(uint32_t logn);
 cudaError_t wide_prepare();
 cudaError_t launch_polymul_wide(const KParams& P, cudaStream_t st, const PhaseEvents* pe);
@@ -113,5 +116,8 @@ cudaError_t launch_check_reduced(const KParams& P, int* d_flag, cudaStream_t st,
 
 // True when the polymul path for this N needs the [nunits][N] scratch.
 inline bool polymul_needs_scratch(uint32_t logn) { return logn >= 14; }
+// True when launch_polymul(P) writes P.s: the three-launch split of two
+// distinct operands (a square keeps its one image in c).
+bool polymul_writes_scratch(const KParams& P);
 
 }  // namespace pm

@@ -880,6 +880,12 @@ cudaError_t launch_polymul(const KParams& P, cudaStream_t st, const PhaseEvents*
   return P.word32 ? launch_polymul_w<uint32_t>(P, st, pe) : launch_polymul_w<uint64_t>(P, st, pe);
 }
 
+bool polymul_writes_scratch(const KParams& P) {
+  if (P.nunits == 0 || !polymul_needs_scratch(P.logn) || P.a == P.b) return false;
+  if (P.row_ops == 4 && wide_polymul_ok(P.logn)) return !wide_single_launch(P.logn, P.nunits);
+  return true;
+}
+
 cudaError_t launch_ntt_fwd(const KParams& P, cudaStream_t st) {
   if (P.row_ops == 4 && wide_ntt_ok(P.logn)) return launch_ntt_fwd_wide(P, st);
   return P.word32 ? launch_ntt_fwd_w<uint32_t>(P, st) : launch_ntt_fwd_w<uint64_t>(P, st);

@@ -882,6 +882,10 @@ cudaError_t wide_prepare_w(bool& clu16) {
 
 bool wide_polymul_ok(uint32_t logn) { return logn >= kWLog && logn <= 17; }
 
+bool wide_single_launch(uint32_t logn, uint32_t nunits) {
+  return logn == kWLog || clustered(logn, nunits);
+}
+
 bool wide_ntt_ok(uint32_t logn) { return logn >= kWLog && logn <= 17; }
 
 cudaError_t wide_prepare() {
