@@ -334,3 +334,24 @@ def test_barrett_alg4_random_60_62_bits(oracle):
                 assert res == (a * b) % q and k <= 1
             for a, b in [(0, 0), (1, q - 1), (q - 1, q - 1)]:
                 assert oracle.barrett(4, a * b, q)[0] == (a * b) % q
+
+
+@pytest.mark.parametrize("nthreads", [1, 3, 4])
+def test_polymul_ntt_batch_limb_rotation(oracle, nthreads):
+    """The batched CPU product (the timing harness of the CPU baseline) is the
+    per-unit product with unit u on limb u mod L, for every thread split
+    (7 units over 3 limbs: with 4 threads the chunks start at units 0, 2, 4,
+    6, i.e. limb offsets 0, 2, 1, 0).  Each unit is also pinned to the
+    schoolbook definition."""
+    log2n, L, U = 6, 3, 7
+    n = 1 << log2n
+    qs = oracle.find_primes(n, L, 60)
+    psis = [oracle.find_psi(q, n) for q in qs]
+    rng = np.random.default_rng(2209)
+    a = np.stack([rng.integers(0, qs[u % L], n, dtype=np.uint64) for u in range(U)])
+    b = np.stack([rng.integers(0, qs[u % L], n, dtype=np.uint64) for u in range(U)])
+    got = oracle.polymul_ntt_batch(a, b, qs, psis, nthreads=nthreads)
+    for u in range(U):
+        q = qs[u % L]
+        assert np.array_equal(got[u], oracle.polymul_ntt(a[u], b[u], q, psis[u % L])), u
+        assert np.array_equal(got[u], oracle.schoolbook(a[u], b[u], q)), u
