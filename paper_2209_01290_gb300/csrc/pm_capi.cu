@@ -82,6 +82,9 @@ struct pm_plan {
   int num_sms = 0;
   uint32_t logn = 0, nlimbs = 0;
   uint32_t flags = 0;
+  // every q < 2^60, 64-bit words, 1/N folded: the 1024-word split may let
+  // values grow to 16q between reductions (KParams::lazy16)
+  bool lazy16 = false;
   std::vector<uint64_t> q, psi;
   pm::LimbConst* d_lc = nullptr;
   pm::TwPair* d_twf = nullptr;
@@ -158,6 +161,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
                               : (row_ctas <= (uint64_t)p->num_sms ? 3u : 2u);
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
   P.word32 = is_word32(p) ? 1 : 0;
+  P.lazy16 = p->lazy16 ? 1 : 0;
   return P;
 }
 
@@ -391,6 +395,9 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   // reinterpreted by the kernels).
   const uint32_t nlc = (flags & PM_PLAN_FUSED) ? 2 * nlimbs : nlimbs;
   const bool halving = (flags & PM_PLAN_HALVING) != 0;
+  p->lazy16 = !word32 && !halving;
+  for (uint32_t l = 0; l < nlimbs; ++l)
+    if (q[l] >> 60) p->lazy16 = false;
   std::vector<pm::LimbConst> lc;
   std::vector<pm::TwPair> twf, twi;
   std::vector<pm::LimbConst32> lc32;
@@ -1044,6 +1051,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   // validate and size
   uint64_t units = 0, scratch = 0;
   int halving = -1, fused = -1;
+  bool lazy16 = true;
   for (uint32_t j = 0; j < njobs; ++j) {
     const pm_job& J = jobs[j];
     if (!J.plan) return fail(PM_ERR_ARG, "job %u: plan is NULL", j);
@@ -1062,6 +1070,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     if (fused >= 0 && f != fused)
       return fail(PM_ERR_ARG, "jobs mix PM_PLAN_FUSED and default plans");
     fused = f;
+    lazy16 = lazy16 && J.plan->lazy16;
     const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
     units += u;
     if (J.plan->logn > 12 && J.a != J.b && !(ext_scratch && ext_scratch[j]))
@@ -1160,6 +1169,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       P.logn = (uint32_t)L;
       P.halving = (uint32_t)halving;
       P.fused = (uint32_t)fused;
+      P.lazy16 = lazy16 ? 1 : 0;
       // N >= 2^13: the 1024-word split (measured faster at every batch
       // size); N = 2^12: whole 4096-word rows with the two-operand kernel
       P.row_ops = L >= 13 ? 4 : 2;

@@ -32,7 +32,8 @@ struct KParams {
                          // half (2/N in place of 1/N) used by the polymul launchers
   uint32_t word32;       // 1: 32-bit words; a/b/c/s hold uint32_t, twf/twi TwPair32,
                          // lc LimbConst32 (the pointers are reinterpreted)
-  uint32_t pad;
+  uint32_t lazy16;       // 1: every q < 2^60 (64-bit words, no halving): the 1024-word
+                         // split lets values grow to 16q between reductions
   const UnitDesc* desc;  // grouped launches (64-bit words): unit u's operands, output,
                          // scratch, tables and constants come from desc[u] instead
 };

@@ -527,13 +527,16 @@ __device__ __forceinline__ void rows_fwd2(W (&va)[16], W (&vb)[16], const W* ga,
 // with three Algorithm 4 products and one Shoup product by Psi_br[..]; the
 // sign (-1)^i is a compile-time choice between u + z and u - z.  This is the
 // first GS stage's output with its 1/2, in [0, 2q).
-template <bool ODD, typename W>
+// With LZ (the wide lazy ranges of the 1024-word rows) the inputs may be
+// anything below 16q.
+template <bool ODD, bool LZ = false, typename W>
 __device__ __forceinline__ void fused_pair(W& x0, W& x1, W y0, W y1,
                                            const typename WordT<W>::Tw& w,
                                            const typename WordT<W>::LC& K) {
   const W q = K.q, two_q = K.two_q;
-  const W a0 = reduce4(x0, q, two_q), a1 = reduce4(x1, q, two_q);
-  const W b0 = reduce4(y0, q, two_q), b1 = reduce4(y1, q, two_q);
+  auto red = [&](W x) { return LZ ? reduce16(x, q, two_q, W(two_q << 2)) : reduce4(x, q, two_q); };
+  const W a0 = red(x0), a1 = red(x1);
+  const W b0 = red(y0), b1 = red(y1);
   const W u = mul_barrett_alg4(a0, b0, K);                                      // [0, q)
   const W v = mul_barrett_alg4(a1, b1, K);                                      // [0, q)
   const W w3 = mul_barrett_alg4(csub(W(a0 + a1), q), csub(W(b0 + b1), q), K);  // [0, q)

@@ -148,12 +148,18 @@ __device__ __forceinline__ void w_geo(int th, int& pbase, int& blk) {
 // positions blk and 2^(2P) + blk).  Pass 0 takes its words from the caller
 // (registers); later passes read their layout from shared memory.  With two operands (TWO) both share the
 // twiddles.  `trunc` omits the transform's last stage (Algorithm 8).
-template <int P, bool TWO, typename W>
+// Ranges: classic (LZ false) reduces x by 2q at every stage, words in
+// [0, 4q); with the wide lazy ranges (LZ) the input may be anything below
+// 16q and only in-row stages 0, 4 and 8 (the first stage of passes 0, 2, 4)
+// reduce x by m = 8q, so words stay below 16q.
+template <int P, bool TWO, bool LZ, typename W>
 __device__ __forceinline__ void w_fwd_pass(W (&va)[4], W (&vb)[4], W* sa, W* sb,
                                            const typename WordT<W>::Tw* tws, int th, W q,
-                                           W two_q, bool trunc) {
+                                           W two_q, W m, bool trunc) {
   using Tw = typename WordT<W>::Tw;
   constexpr int E = kWLog - 2 - 2 * P;
+  constexpr bool R0 = !LZ || (P % 2 == 0);  // in-row stage 2P
+  constexpr bool R1 = !LZ;                  // in-row stage 2P + 1
   int pb, blk;
   w_geo<W, E>(th, pb, blk);
   if constexpr (P > 0) {
@@ -161,20 +167,20 @@ __device__ __forceinline__ void w_fwd_pass(W (&va)[4], W (&vb)[4], W* sa, W* sb,
     if constexpr (TWO) lat_ld<W, E>(vb, sb, pb);
   }
   const Tw t0 = tws[(1 << (2 * P)) - 1 + blk];
-  ct_bfly(va[0], va[2], t0.w, t0.wp, q, two_q);
-  ct_bfly(va[1], va[3], t0.w, t0.wp, q, two_q);
+  ct_bfly_m<R0>(va[0], va[2], t0.w, t0.wp, q, two_q, m);
+  ct_bfly_m<R0>(va[1], va[3], t0.w, t0.wp, q, two_q, m);
   if constexpr (TWO) {
-    ct_bfly(vb[0], vb[2], t0.w, t0.wp, q, two_q);
-    ct_bfly(vb[1], vb[3], t0.w, t0.wp, q, two_q);
+    ct_bfly_m<R0>(vb[0], vb[2], t0.w, t0.wp, q, two_q, m);
+    ct_bfly_m<R0>(vb[1], vb[3], t0.w, t0.wp, q, two_q, m);
   }
   if (!(P == kWPasses - 1 && trunc)) {
     const Tw* t1 = tws + (1 << (2 * P + 1)) - 1 + blk;  // odd slice: evens, then odds
     const Tw t1a = t1[0], t1b = t1[1 << (2 * P)];
-    ct_bfly(va[0], va[1], t1a.w, t1a.wp, q, two_q);
-    ct_bfly(va[2], va[3], t1b.w, t1b.wp, q, two_q);
+    ct_bfly_m<R1>(va[0], va[1], t1a.w, t1a.wp, q, two_q, m);
+    ct_bfly_m<R1>(va[2], va[3], t1b.w, t1b.wp, q, two_q, m);
     if constexpr (TWO) {
-      ct_bfly(vb[0], vb[1], t1a.w, t1a.wp, q, two_q);
-      ct_bfly(vb[2], vb[3], t1b.w, t1b.wp, q, two_q);
+      ct_bfly_m<R1>(vb[0], vb[1], t1a.w, t1a.wp, q, two_q, m);
+      ct_bfly_m<R1>(vb[2], vb[3], t1b.w, t1b.wp, q, two_q, m);
     }
   }
   if constexpr (P < kWPasses - 1) {
@@ -185,68 +191,96 @@ __device__ __forceinline__ void w_fwd_pass(W (&va)[4], W (&vb)[4], W* sa, W* sb,
 }
 
 // Forward in-row stages; leaves the last layout (thread th holds words
-// 4 th .. 4 th + 3, bit-reversed order, lazy in [0, 4q)) in va (and vb).
-template <bool TWO, typename W>
+// 4 th .. 4 th + 3, bit-reversed order, lazy: below 4q, or 16q with LZ) in
+// va (and vb).
+template <bool TWO, bool LZ = false, typename W>
 __device__ __forceinline__ void w_fwd(W (&va)[4], W (&vb)[4], W* sa, W* sb,
                                       const typename WordT<W>::Tw* tws, int th, W q, W two_q,
                                       bool trunc) {
-  w_fwd_pass<0, TWO>(va, vb, sa, sb, tws, th, q, two_q, trunc);
-  w_fwd_pass<1, TWO>(va, vb, sa, sb, tws, th, q, two_q, trunc);
-  w_fwd_pass<2, TWO>(va, vb, sa, sb, tws, th, q, two_q, trunc);
-  w_fwd_pass<3, TWO>(va, vb, sa, sb, tws, th, q, two_q, trunc);
-  w_fwd_pass<4, TWO>(va, vb, sa, sb, tws, th, q, two_q, trunc);
+  const W m = LZ ? W(two_q << 2) : two_q;
+  w_fwd_pass<0, TWO, LZ>(va, vb, sa, sb, tws, th, q, two_q, m, trunc);
+  w_fwd_pass<1, TWO, LZ>(va, vb, sa, sb, tws, th, q, two_q, m, trunc);
+  w_fwd_pass<2, TWO, LZ>(va, vb, sa, sb, tws, th, q, two_q, m, trunc);
+  w_fwd_pass<3, TWO, LZ>(va, vb, sa, sb, tws, th, q, two_q, m, trunc);
+  w_fwd_pass<4, TWO, LZ>(va, vb, sa, sb, tws, th, q, two_q, m, trunc);
+}
+
+// The forward rows' output (below 4q, or 16q with LZ) to [0, q).
+template <bool LZ, typename W>
+__device__ __forceinline__ W w_reduce_out(W x, W q, W two_q) {
+  if constexpr (LZ)
+    return reduce16(x, q, two_q, W(two_q << 2));
+  else
+    return reduce4(x, q, two_q);
 }
 
 // One inverse pass PI on the layout of forward pass PF = 4 - PI: GS stage
 // 2 PI pairs (u, u+1) with slice 2 PF + 1's entries 2 blk + u/2, GS stage
 // 2 PI + 1 pairs (u, u+2) with slice 2 PF's entry blk.  The first pass works
 // on the registers it is given; `trunc` omits its first stage (Algorithm 8).
-template <int PI, bool HALVE, typename W>
+// Ranges: classic words in [0, 2q); with LZ (input below 2q) words stay
+// below 8q: in-row GS stages 0..2 leave their sums unreduced, later ones
+// reduce them by 8q.
+template <int PI, bool HALVE, bool LZ, typename W>
 __device__ __forceinline__ void w_inv_pass(W (&v)[4], W* s, const typename WordT<W>::Tw* tws,
-                                           int th, W q, W two_q, W hq, bool trunc) {
+                                           int th, W q, W two_q, W hq, W m, bool trunc) {
   using Tw = typename WordT<W>::Tw;
+  static_assert(!(LZ && HALVE), "wide lazy ranges fold 1/N at the end");
   constexpr int PF = kWPasses - 1 - PI;
   constexpr int E = kWLog - 2 - 2 * PF;
+  constexpr bool R0 = 2 * PI >= 3, R1 = 2 * PI + 1 >= 3;
   int pb, blk;
   w_geo<W, E>(th, pb, blk);
   if constexpr (PI > 0) lat_ld<W, E>(v, s, pb);
   if (!(PI == 0 && trunc)) {
     const Tw* t0 = tws + (1 << (2 * PF + 1)) - 1 + blk;  // odd slice: evens, then odds
     const Tw t0a = t0[0], t0b = t0[1 << (2 * PF)];
-    gs_bfly_mode<HALVE>(v[0], v[1], t0a.w, t0a.wp, q, two_q, hq);
-    gs_bfly_mode<HALVE>(v[2], v[3], t0b.w, t0b.wp, q, two_q, hq);
+    if constexpr (LZ) {
+      gs_bfly_m<R0>(v[0], v[1], t0a.w, t0a.wp, q, m);
+      gs_bfly_m<R0>(v[2], v[3], t0b.w, t0b.wp, q, m);
+    } else {
+      gs_bfly_mode<HALVE>(v[0], v[1], t0a.w, t0a.wp, q, two_q, hq);
+      gs_bfly_mode<HALVE>(v[2], v[3], t0b.w, t0b.wp, q, two_q, hq);
+    }
   }
   const Tw t1 = tws[(1 << (2 * PF)) - 1 + blk];
-  gs_bfly_mode<HALVE>(v[0], v[2], t1.w, t1.wp, q, two_q, hq);
-  gs_bfly_mode<HALVE>(v[1], v[3], t1.w, t1.wp, q, two_q, hq);
+  if constexpr (LZ) {
+    gs_bfly_m<R1>(v[0], v[2], t1.w, t1.wp, q, m);
+    gs_bfly_m<R1>(v[1], v[3], t1.w, t1.wp, q, m);
+  } else {
+    gs_bfly_mode<HALVE>(v[0], v[2], t1.w, t1.wp, q, two_q, hq);
+    gs_bfly_mode<HALVE>(v[1], v[3], t1.w, t1.wp, q, two_q, hq);
+  }
   if constexpr (PI < kWPasses - 1) {
     lat_st<W, E>(s, pb, v);
     __syncthreads();
   }
 }
 
-// Inverse in-row stages; leaves words th + 256 u of the row (lazy, [0, 2q))
-// in v.
-template <bool HALVE, typename W>
+// Inverse in-row stages; leaves words th + 256 u of the row (lazy: below 2q,
+// or 8q with LZ) in v.
+template <bool HALVE, bool LZ = false, typename W>
 __device__ __forceinline__ void w_inv_passes(W (&v)[4], W* s, const typename WordT<W>::Tw* tws,
                                              int th, const typename WordT<W>::LC& K, bool trunc) {
   const W q = K.q, two_q = K.two_q, hq = K.half_q1;
-  w_inv_pass<0, HALVE>(v, s, tws, th, q, two_q, hq, trunc);
-  w_inv_pass<1, HALVE>(v, s, tws, th, q, two_q, hq, trunc);
-  w_inv_pass<2, HALVE>(v, s, tws, th, q, two_q, hq, trunc);
-  w_inv_pass<3, HALVE>(v, s, tws, th, q, two_q, hq, trunc);
-  w_inv_pass<4, HALVE>(v, s, tws, th, q, two_q, hq, trunc);
+  const W m = LZ ? W(two_q << 2) : two_q;
+  w_inv_pass<0, HALVE, LZ>(v, s, tws, th, q, two_q, hq, m, trunc);
+  w_inv_pass<1, HALVE, LZ>(v, s, tws, th, q, two_q, hq, m, trunc);
+  w_inv_pass<2, HALVE, LZ>(v, s, tws, th, q, two_q, hq, m, trunc);
+  w_inv_pass<3, HALVE, LZ>(v, s, tws, th, q, two_q, hq, m, trunc);
+  w_inv_pass<4, HALVE, LZ>(v, s, tws, th, q, two_q, hq, m, trunc);
 }
 
 // Inverse in-row stages; the result (words th + 256 u of the row) goes to
 // g_dst: canonical, times N^-1 unless every stage halves, when `final` (the
-// row is the whole transform), else lazy in [0, 2q) for k_wcol_inv.
-template <bool HALVE, typename W>
+// row is the whole transform), else lazy (below 2q, or 8q with LZ) for
+// k_wcol_inv.
+template <bool HALVE, bool LZ, typename W>
 __device__ __forceinline__ void w_inv(W (&v)[4], W* g_dst, bool final, W* s,
                                       const typename WordT<W>::Tw* tws, int th,
                                       const typename WordT<W>::LC& K, bool trunc) {
   const W q = K.q;
-  w_inv_passes<HALVE>(v, s, tws, th, K, trunc);
+  w_inv_passes<HALVE, LZ>(v, s, tws, th, K, trunc);
   if (!HALVE && final) {
 #pragma unroll
     for (int u = 0; u < 4; u++) v[u] = mul_shoup_lazy(v[u], K.ninv, K.ninv_p, q);
@@ -299,7 +333,9 @@ struct WUnit {
 // column images of a and b from c and s (n > 10) or a and b themselves
 // (n = 10); forward NTT rows read c in natural order and write it
 // bit-reversed and canonical; inverse NTT rows read c bit-reversed.
-template <int MODE, bool HALVE, typename W, bool DESC = false>
+// LZ: the wide lazy ranges (64-bit words, q < 2^60, no per-stage halving):
+// the column images arrive below 16q, the inverse output leaves below 8q.
+template <int MODE, bool HALVE, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   using Tw = typename WordT<W>::Tw;
   extern __shared__ __align__(16) uint64_t smem_raw[];
@@ -347,22 +383,24 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   cp_async_wait_all();
   __syncthreads();
   if constexpr (MODE == MODE_INV) {
-    w_inv<HALVE>(va, U.c + off, single, sa, tw_i, th, K, false);
+    w_inv<HALVE, LZ>(va, U.c + off, single, sa, tw_i, th, K, false);
   } else if constexpr (MODE == MODE_FWD) {
-    w_fwd<false>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, false);
+    w_fwd<false, LZ>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, false);
 #pragma unroll
-    for (int u = 0; u < 4; u++) __stcs(U.c + off + 4 * th + u, reduce4(va[u], K.q, K.two_q));
+    for (int u = 0; u < 4; u++)
+      __stcs(U.c + off + 4 * th + u, w_reduce_out<LZ>(va[u], K.q, K.two_q));
   } else {
-    w_fwd<true>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, kFused);
+    w_fwd<true, LZ>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, kFused);
     if constexpr (kFused) {
-      fused_pair<false>(va[0], va[1], vb[0], vb[1], wf, K);
-      fused_pair<true>(va[2], va[3], vb[2], vb[3], wf, K);
+      fused_pair<false, LZ>(va[0], va[1], vb[0], vb[1], wf, K);
+      fused_pair<true, LZ>(va[2], va[3], vb[2], vb[3], wf, K);
     } else {
 #pragma unroll
       for (int u = 0; u < 4; u++)
-        va[u] = mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
+        va[u] = mul_barrett_alg4(w_reduce_out<LZ>(va[u], K.q, K.two_q),
+                                 w_reduce_out<LZ>(vb[u], K.q, K.two_q), K);
     }
-    w_inv<HALVE>(va, U.c + off, single, sa, tw_i, th, K, kFused);
+    w_inv<HALVE, LZ>(va, U.c + off, single, sa, tw_i, th, K, kFused);
   }
 }
 
@@ -380,7 +418,7 @@ struct WCol {
 // consecutive column words held in x (group m is block g0 + m at stage 4):
 // stage 4 + D pairs words G/2^(D+1) apart with twiddle
 // Psi_br[2^(4+D) + (g0 + m) 2^D + b] for block b of the group.
-template <int G, int D, typename W>
+template <int G, int D, bool RED, typename W>
 __device__ __forceinline__ void ct_tail(W (&x)[16], const typename WordT<W>::Tw* __restrict__ tw,
                                         uint32_t g0, W q, W two_q) {
   if constexpr ((1 << D) < G) {
@@ -393,9 +431,10 @@ __device__ __forceinline__ void ct_tail(W (&x)[16], const typename WordT<W>::Tw*
         const auto w = ld_tw(tw + (1u << (4 + D)) + ((g0 + m) << D) + b);
 #pragma unroll
         for (int u0 = 0; u0 < h; u0++)
-          ct_bfly(x[G * m + 2 * h * b + u0], x[G * m + 2 * h * b + u0 + h], w.w, w.wp, q, two_q);
+          ct_bfly_m<RED>(x[G * m + 2 * h * b + u0], x[G * m + 2 * h * b + u0 + h], w.w, w.wp, q,
+                         two_q, two_q);
       }
-    ct_tail<G, D + 1>(x, tw, g0, q, two_q);
+    ct_tail<G, D + 1, RED>(x, tw, g0, q, two_q);
   }
 }
 
@@ -404,7 +443,7 @@ __device__ __forceinline__ void ct_tail(W (&x)[16], const typename WordT<W>::Tw*
 // consecutive words held in x (group m = column words G (g0 + m) ...): the
 // pair (t, t + 2^D) takes Psi^-1_br[(R >> (D+1)) + (t >> (D+1))] with
 // R = 16 G.
-template <int G, int D, bool HALVE, typename W>
+template <int G, int D, bool HALVE, bool LZ, typename W>
 __device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw* __restrict__ tw,
                                         uint32_t g0, const typename WordT<W>::LC& K) {
   if constexpr ((1 << D) < G) {
@@ -417,11 +456,16 @@ __device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw*
         const uint32_t idx = ((16u * G) >> (D + 1)) + (g0 + m) * (uint32_t)nb + b;
         const auto w = ld_tw(tw + idx);
 #pragma unroll
-        for (int u0 = 0; u0 < h; u0++)
-          gs_bfly_mode<HALVE>(x[G * m + 2 * h * b + u0], x[G * m + 2 * h * b + u0 + h], w.w, w.wp,
-                              K.q, K.two_q, K.half_q1);
+        for (int u0 = 0; u0 < h; u0++) {
+          W& lo = x[G * m + 2 * h * b + u0];
+          W& hi = x[G * m + 2 * h * b + u0 + h];
+          if constexpr (LZ)
+            gs_bfly_m<true>(lo, hi, w.w, w.wp, K.q, W(K.two_q << 2));
+          else
+            gs_bfly_mode<HALVE>(lo, hi, w.w, w.wp, K.q, K.two_q, K.half_q1);
+        }
       }
-    gs_tail<G, D + 1, HALVE>(x, tw, g0, K);
+    gs_tail<G, D + 1, HALVE, LZ>(x, tw, g0, K);
   }
 }
 
@@ -429,7 +473,9 @@ __device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw*
 // (a) goes to c, operand 1 (b) to the scratch s.  Every word of a column is
 // read (before the barrier) and written (after it) by the CTA that owns the
 // column, so c may alias a.
-template <int CL, typename W, bool DESC = false>
+// LZ: wide lazy ranges, no reduction at all (canonical input, CL <= 7
+// stages: images below (1 + 2 CL) q <= 15q).
+template <int CL, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) {
   using S = WCol<CL>;
   const uint32_t tile = blockIdx.x % S::kTiles;
@@ -448,7 +494,7 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) 
   W x[S::M];
 #pragma unroll
   for (int k = 0; k < S::M; k++) x[k] = __ldcs(src + (size_t)(j + S::J * k) * kW);
-  ct_col<S::M>(x, twf, K.q, K.two_q);
+  ct_col<S::M, W, !LZ>(x, twf, K.q, K.two_q);
   if constexpr (S::J > 1) {
     __shared__ W tile_s[S::R * S::CT];
 #pragma unroll
@@ -456,7 +502,7 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) 
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < S::M; i++) x[i] = tile_s[(S::M * j + i) * S::CT + c];
-    ct_tail<S::J, 0>(x, twf, (uint32_t)(S::M / S::J * j), K.q, K.two_q);
+    ct_tail<S::J, 0, !LZ>(x, twf, (uint32_t)(S::M / S::J * j), K.q, K.two_q);
 #pragma unroll
     for (int i = 0; i < S::M; i++) dst[(size_t)(S::M * j + i) * kW] = x[i];
   } else {
@@ -467,7 +513,8 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) 
 
 // Inverse column stages and the reduction, in place on c: the rows' lazy
 // output [0, 2q) in, canonical words out.
-template <int CL, bool HALVE, typename W, bool DESC = false>
+// LZ: wide lazy ranges (rows' output below 8q; every sum reduced by 8q).
+template <int CL, bool HALVE, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   using S = WCol<CL>;
   const uint32_t tile = blockIdx.x % S::kTiles;
@@ -483,7 +530,7 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   if constexpr (S::J > 1) {
 #pragma unroll
     for (int i = 0; i < S::M; i++) x[i] = p[(size_t)(S::M * j + i) * kW];
-    gs_tail<S::J, 0, HALVE>(x, twi, (uint32_t)(S::M / S::J * j), K);
+    gs_tail<S::J, 0, HALVE, LZ>(x, twi, (uint32_t)(S::M / S::J * j), K);
     __shared__ W tile_s[S::R * S::CT];
 #pragma unroll
     for (int i = 0; i < S::M; i++) tile_s[(S::M * j + i) * S::CT + c] = x[i];
@@ -496,7 +543,7 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   }
   // the last four (or all CL) stages: words t = j + J k, the pair distance
   // J 2^E' in t is 2^E' in k and the twiddle index reduces to gs_col's
-  gs_col<S::M, HALVE>(x, twi, K);
+  gs_col<S::M, HALVE, W, LZ>(x, twi, K);
 #pragma unroll
   for (int k = 0; k < S::M; k++) __stcs(p + (size_t)(j + S::J * k) * kW, csub(x[k], K.q));
 }
@@ -605,11 +652,20 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
 
 // ------------------------------------------------------------ launchers
 
+// The wide lazy ranges apply to 64-bit words with every q < 2^60 and the
+// 1/N fold (the host sets P.lazy16 only then).
+template <typename W>
+inline bool use_lazy16(const KParams& P) {
+  return sizeof(W) == 8 && P.lazy16 && !P.halving;
+}
+
 template <int MODE, typename W>
 cudaError_t wrows(const KParams& P, cudaStream_t st) {
   const size_t blocks = (size_t)P.nunits << (P.logn - kWLog);
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
-  if (P.halving)
+  if (use_lazy16<W>(P))
+    k_wrows<MODE, false, W, false, true><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
+  else if (P.halving)
     k_wrows<MODE, true, W><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
   else
     k_wrows<MODE, false, W><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
@@ -620,7 +676,10 @@ template <int CL, typename W>
 cudaError_t wcol_fwd_cl(const KParams& P, int nops, cudaStream_t st) {
   const size_t blocks = (size_t)P.nunits * nops * WCol<CL>::kTiles;
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
-  k_wcol_fwd<CL, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, nops);
+  if (use_lazy16<W>(P))
+    k_wcol_fwd<CL, W, false, true><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, nops);
+  else
+    k_wcol_fwd<CL, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, nops);
   return cudaGetLastError();
 }
 
@@ -628,7 +687,9 @@ template <int CL, typename W>
 cudaError_t wcol_inv_cl(const KParams& P, cudaStream_t st) {
   const size_t blocks = (size_t)P.nunits * WCol<CL>::kTiles;
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
-  if (P.halving)
+  if (use_lazy16<W>(P))
+    k_wcol_inv<CL, false, W, false, true><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
+  else if (P.halving)
     k_wcol_inv<CL, true, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
   else
     k_wcol_inv<CL, false, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
@@ -791,7 +852,7 @@ cudaError_t prepare_clu() {
 // Grouped uneven launch (64-bit words): the units of one N >= 2^13 through
 // the three wide-split kernels, each unit's rows, scratch, tables and
 // constants (the fused ones for an Algorithm 8 plan) from P.desc.
-template <int CL, bool H, bool F>
+template <int CL, bool H, bool F, bool LZ>
 cudaError_t wide_desc_cl(const KParams& P, cudaStream_t st) {
   using W = uint64_t;
   constexpr int MODE = F ? MODE_POLYMUL_FUSED : MODE_POLYMUL;
@@ -799,20 +860,25 @@ cudaError_t wide_desc_cl(const KParams& P, cudaStream_t st) {
   const size_t rows = (size_t)P.nunits << CL;
   const size_t inv = (size_t)P.nunits * WCol<CL>::kTiles;
   if (cols > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
-  k_wcol_fwd<CL, W, true><<<(unsigned)cols, kWColThreads, 0, st>>>(P, 2);
+  k_wcol_fwd<CL, W, true, LZ><<<(unsigned)cols, kWColThreads, 0, st>>>(P, 2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_wrows<MODE, H, W, true><<<(unsigned)rows, kWThreads, kWRowsSmem<W>, st>>>(P);
+  k_wrows<MODE, H, W, true, LZ><<<(unsigned)rows, kWThreads, kWRowsSmem<W>, st>>>(P);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_wcol_inv<CL, H, W, true><<<(unsigned)inv, kWColThreads, 0, st>>>(P);
+  k_wcol_inv<CL, H, W, true, LZ><<<(unsigned)inv, kWColThreads, 0, st>>>(P);
   return cudaGetLastError();
 }
 
 template <int CL>
 cudaError_t wide_desc(const KParams& P, cudaStream_t st) {
   if (P.halving)
-    return P.fused ? wide_desc_cl<CL, true, true>(P, st) : wide_desc_cl<CL, true, false>(P, st);
-  return P.fused ? wide_desc_cl<CL, false, true>(P, st) : wide_desc_cl<CL, false, false>(P, st);
+    return P.fused ? wide_desc_cl<CL, true, true, false>(P, st)
+                   : wide_desc_cl<CL, true, false, false>(P, st);
+  if (P.lazy16)
+    return P.fused ? wide_desc_cl<CL, false, true, true>(P, st)
+                   : wide_desc_cl<CL, false, false, true>(P, st);
+  return P.fused ? wide_desc_cl<CL, false, true, false>(P, st)
+                 : wide_desc_cl<CL, false, false, false>(P, st);
 }
 
 // Clusters of 16 CTAs for N = 2^14: allowed (non-portable size) and
@@ -873,6 +939,19 @@ cudaError_t wide_prepare_w(bool& clu16) {
       if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kWRowsSmem<W>)) != cudaSuccess)
         return e;
+    }
+    if constexpr (!H) {  // the wide lazy ranges: 64-bit words, 1/N folded
+      const void* lz_fns[] = {(const void*)k_wrows<MODE_POLYMUL, H, W, false, true>,
+                              (const void*)k_wrows<MODE_POLYMUL_FUSED, H, W, false, true>,
+                              (const void*)k_wrows<MODE_FWD, H, W, false, true>,
+                              (const void*)k_wrows<MODE_INV, H, W, false, true>,
+                              (const void*)k_wrows<MODE_POLYMUL, H, W, true, true>,
+                              (const void*)k_wrows<MODE_POLYMUL_FUSED, H, W, true, true>};
+      for (const void* f : lz_fns) {
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kWRowsSmem<W>)) != cudaSuccess)
+          return e;
+      }
     }
   }
   return cudaSuccess;
