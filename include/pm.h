@@ -7,8 +7,9 @@
  * i.e. a merged Cooley-Tukey forward NTT (Algorithm 6), a pointwise product
  * reduced with the paper's Barrett variant (Algorithm 4), and a merged
  * Gentleman-Sande inverse NTT (Algorithm 7) with the 1/N scaling folded into
- * its butterflies as halvings (Sec. III-A).  Many independent products (RNS
- * limbs x polynomials) run in one launch.
+ * its last stage (or, with PM_PLAN_HALVING, into every butterfly as the
+ * halvings of Sec. III-A).  Many independent products (RNS limbs x
+ * polynomials) run in one call.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -390,14 +391,19 @@ pm_status pm_plan_get_tuning(const pm_plan *plan, pm_tuning *t);
  * work.  PM_ERR_ARG for a NULL tuning or an invalid batch size. */
 pm_status pm_plan_resolve_tuning(const pm_plan *plan, uint32_t npoly, pm_tuning *t);
 
-/* Test hook: fault injection on the host side of the next persistent
- * polymul launch on this plan (kind 0 clears it).
- *   PM_FAULT_WITHHOLD_SIGNAL : the launch's row tasks wait for one more
- *     "column stage done" signal than will ever arrive, so their bounded
- *     waits run out (about a second); pm_plan_sync then reports
- *     PM_ERR_TIMEOUT and the results of that call are invalid.  Nothing
- *     faults on the device and later calls work normally. */
-enum { PM_FAULT_WITHHOLD_SIGNAL = 1 };
+/* Test hook: fault injection on the host side of the next polymul launch
+ * on this plan (kind 0 clears it).
+ *   PM_FAULT_WITHHOLD_SIGNAL : (next persistent launch) the row tasks wait
+ *     for one more "column stage done" signal than will ever arrive, so
+ *     their bounded waits run out (about a second); pm_plan_sync then
+ *     reports PM_ERR_TIMEOUT and the results of that call are invalid.
+ *   PM_FAULT_SHORT_TWIDDLES : (next split launch with 64-bit words, N >=
+ *     2^10) every row CTA's barrier expects 16 bytes more than its bulk
+ *     twiddle copies deliver, so its bounded wait runs out (about a second
+ *     per CTA, twice); pm_plan_sync reports PM_ERR_TIMEOUT and the results of
+ *     that call are invalid.
+ * Nothing faults on the device and later calls work normally. */
+enum { PM_FAULT_WITHHOLD_SIGNAL = 1, PM_FAULT_SHORT_TWIDDLES = 2 };
 pm_status pm_plan_inject_fault(pm_plan *plan, int kind);
 
 /* Profiling hook for pm_polymul: with n > 0, each later pm_polymul on this

@@ -265,6 +265,7 @@ def pm_plan_autotune(plan: int, npoly: int, stream: int = 0):
 
 
 PM_FAULT_WITHHOLD_SIGNAL = 1
+PM_FAULT_SHORT_TWIDDLES = 2
 
 
 def pm_plan_inject_fault(plan: int, kind: int) -> None:

@@ -86,24 +86,27 @@ __device__ __forceinline__ W mul_shoup_lazy(W y, W w, W wp, W q) {
 __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint64_t wp,
                                                    uint64_t q) {
   const uint64_t nq = 0 - q;
-  uint32_t m1, m2, m3, q0, q1, r0, r1;
-  asm("mul.hi.u32      %0, %9, %7;\n\t"      // m1 = hi(p0 y0)
-      "mad.lo.cc.u32   %0, %10, %7, %0;\n\t"  // m1 += lo(p1 y0)
-      "madc.hi.u32     %1, %10, %7, 0;\n\t"   // m2 = hi(p1 y0) + carry
-      "mad.lo.cc.u32   %0, %9, %8, %0;\n\t"   // m1 += lo(p0 y1)
-      "madc.hi.cc.u32  %1, %9, %8, %1;\n\t"   // m2 += hi(p0 y1) + carry
-      "addc.u32        %2, 0, 0;\n\t"         // m3 = carry
-      "mad.lo.cc.u32   %3, %10, %8, %1;\n\t"  // q0 = lo(p1 y1) + m2
-      "madc.hi.u32     %4, %10, %8, %2;\n\t"  // q1 = hi(p1 y1) + m3 + carry
-      "mul.lo.u32      %5, %11, %7;\n\t"      // r = w y mod 2^64
-      "mul.hi.u32      %6, %11, %7;\n\t"
-      "mad.lo.u32      %6, %12, %7, %6;\n\t"
-      "mad.lo.u32      %6, %11, %8, %6;\n\t"
-      "mad.lo.cc.u32   %5, %3, %13, %5;\n\t"  // r += qh (2^64 - q) mod 2^64
-      "madc.hi.u32     %6, %3, %13, %6;\n\t"
-      "mad.lo.u32      %6, %4, %13, %6;\n\t"
-      "mad.lo.u32      %6, %3, %14, %6;"
-      : "=&r"(m1), "=&r"(m2), "=&r"(m3), "=&r"(q0), "=&r"(q1), "=&r"(r0), "=&r"(r1)
+  uint32_t r0, r1;
+  asm("{\n\t"
+      ".reg .u32 m1, m2, m3, q0, q1;\n\t"
+      "mul.hi.u32      m1, %4, %2;\n\t"      // m1 = hi(p0 y0)
+      "mad.lo.cc.u32   m1, %5, %2, m1;\n\t"  // m1 += lo(p1 y0)
+      "madc.hi.u32     m2, %5, %2, 0;\n\t"   // m2 = hi(p1 y0) + carry
+      "mad.lo.cc.u32   m1, %4, %3, m1;\n\t"  // m1 += lo(p0 y1)
+      "madc.hi.cc.u32  m2, %4, %3, m2;\n\t"  // m2 += hi(p0 y1) + carry
+      "addc.u32        m3, 0, 0;\n\t"        // m3 = carry
+      "mad.lo.cc.u32   q0, %5, %3, m2;\n\t"  // q0 = lo(p1 y1) + m2
+      "madc.hi.u32     q1, %5, %3, m3;\n\t"  // q1 = hi(p1 y1) + m3 + carry
+      "mul.lo.u32      %0, %6, %2;\n\t"      // r = w y mod 2^64
+      "mul.hi.u32      %1, %6, %2;\n\t"
+      "mad.lo.u32      %1, %7, %2, %1;\n\t"
+      "mad.lo.u32      %1, %6, %3, %1;\n\t"
+      "mad.lo.cc.u32   %0, q0, %8, %0;\n\t"  // r += qh (2^64 - q) mod 2^64
+      "madc.hi.u32     %1, q0, %8, %1;\n\t"
+      "mad.lo.u32      %1, q1, %8, %1;\n\t"
+      "mad.lo.u32      %1, q0, %9, %1;\n\t"
+      "}"
+      : "=&r"(r0), "=&r"(r1)
       : "r"((uint32_t)y), "r"((uint32_t)(y >> 32)), "r"((uint32_t)wp),
         "r"((uint32_t)(wp >> 32)), "r"((uint32_t)w), "r"((uint32_t)(w >> 32)),
         "r"((uint32_t)nq), "r"((uint32_t)(nq >> 32)));

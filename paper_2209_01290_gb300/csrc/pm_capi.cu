@@ -90,6 +90,7 @@ struct pm_plan {
   pm::TwPair* d_twf = nullptr;
   pm::TwPair* d_twi = nullptr;
   int* d_flag = nullptr;
+  int* d_err = nullptr;  // set by a row CTA whose bounded wait for its twiddles gave up
   std::mutex mu;  // guards the scratch list and the host-pipeline objects
   // Scratch for the column-split polymul path, one area per stream so that
   // calls on different streams never share it (calls on one stream are
@@ -162,6 +163,7 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
   P.word32 = is_word32(p) ? 1 : 0;
   P.lazy16 = p->lazy16 ? 1 : 0;
+  P.err = p->d_err;
   return P;
 }
 
@@ -231,6 +233,7 @@ void destroy_plan(pm_plan* p) {
   cudaFree(p->d_twf);
   cudaFree(p->d_twi);
   cudaFree(p->d_flag);
+  cudaFree(p->d_err);
   for (auto& sc : p->scratch) {
     cudaFree(sc.ptr);
     cudaFree(sc.ctl);
@@ -276,6 +279,10 @@ pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uin
   if (pm::polymul_needs_scratch(p->logn)) {
     pm_status s = ensure_scratch(p, st, P.nunits, &P.s);
     if (s != PM_OK) return s;
+  }
+  if (p->inject == PM_FAULT_SHORT_TWIDDLES) {
+    P.inject_tx = 16;
+    p->inject = 0;
   }
   e = pm::launch_polymul(P, st, pe);
   if (e != cudaSuccess) return cuda_fail(e, "polymul launch");
@@ -439,6 +446,8 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   if (e == cudaSuccess) e = cudaMalloc(&d_twi, tw_bytes);
   p->d_twi = (pm::TwPair*)d_twi;
   if (e == cudaSuccess) e = cudaMalloc(&p->d_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (e != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "cudaMalloc(plan tables)");
@@ -830,6 +839,13 @@ pm_status pm_plan_sync(const pm_plan* plan, void* stream) {
   // a persistent launch on this stream that gave up waiting leaves a flag
   pm_plan* p = const_cast<pm_plan*>(plan);
   std::lock_guard<std::mutex> lk(p->mu);
+  int rflag = 0;
+  if ((e = cudaMemcpy(&rflag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read status");
+  if (rflag) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(PM_ERR_TIMEOUT, "a row kernel gave up waiting for its staged twiddles");
+  }
   for (auto& sc : p->scratch) {
     if (sc.stream != (cudaStream_t)stream || !sc.ctl) continue;
     uint32_t flag = 0;
@@ -934,7 +950,8 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
 pm_status pm_plan_inject_fault(pm_plan* plan, int kind) {
   pm_status s = check_plan(plan);
   if (s != PM_OK) return s;
-  if (kind != 0 && kind != PM_FAULT_WITHHOLD_SIGNAL) return fail(PM_ERR_ARG, "unknown fault %d", kind);
+  if (kind != 0 && kind != PM_FAULT_WITHHOLD_SIGNAL && kind != PM_FAULT_SHORT_TWIDDLES)
+    return fail(PM_ERR_ARG, "unknown fault %d", kind);
   std::lock_guard<std::mutex> lk(plan->mu);
   plan->inject = kind;
   return ok();
@@ -1170,6 +1187,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       P.halving = (uint32_t)halving;
       P.fused = (uint32_t)fused;
       P.lazy16 = lazy16 ? 1 : 0;
+      P.err = reinterpret_cast<int*>(q->d_ctl + 1);  // reported by pm_queue_sync
       // N >= 2^13: the 1024-word split (measured faster at every batch
       // size); N = 2^12: whole 4096-word rows with the two-operand kernel
       P.row_ops = L >= 13 ? 4 : 2;

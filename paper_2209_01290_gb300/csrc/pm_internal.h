@@ -36,6 +36,10 @@ struct KParams {
                          // split lets values grow to 16q between reductions
   const UnitDesc* desc;  // grouped launches (64-bit words): unit u's operands, output,
                          // scratch, tables and constants come from desc[u] instead
+  int* err;              // device flag: set (to 1) by a CTA whose bounded wait for its
+                         // staged twiddles gave up (NULL: not recorded)
+  uint32_t inject_tx;    // test hook: extra bytes each row CTA's barrier expects (0)
+  uint32_t pad2;
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the

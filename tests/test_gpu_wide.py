@@ -189,3 +189,27 @@ def test_resolved_row_kernel_rule():
         assert capi.pm_plan_resolve_tuning(plan.handle, npoly).row_ops == 1
     with pytest.raises(capi.PMError):
         capi.pm_plan_resolve_tuning(plan.handle, 0)
+
+
+def test_short_twiddles_times_out_then_recovers(oracle):
+    """Host-side fault injection on the bulk-copy wait of the row kernel:
+    every row CTA's barrier expects 16 bytes more than its twiddle copies
+    deliver, so each bounded wait gives up after about a second and the CTA
+    skips its row; pm_plan_sync reports PM_ERR_TIMEOUT.  The next call is
+    correct and reports no error."""
+    import time
+    from paper_2209_01290_gb300 import capi
+    plan, qs, psis = _plan(16, 1)
+    a, b = operands(77000, qs, 1, 1 << 16)
+    want = oracle_polymul_batch(oracle, a, b, qs, psis)
+    da, db = to_dev(a), to_dev(b)
+    capi.pm_plan_inject_fault(plan.handle, capi.PM_FAULT_SHORT_TWIDDLES)
+    t0 = time.time()
+    plan.polymul(da, db)
+    with pytest.raises(capi.PMError) as e:
+        plan.sync()
+    assert e.value.status == -7
+    assert time.time() - t0 < 30
+    got = to_host(plan.polymul(da, db))
+    plan.sync()
+    assert np.array_equal(got, want)

@@ -9,8 +9,9 @@ the index formulas restated from the kernel sources:
 * the twiddle slices a 1024-word row stages in shared memory: every entry of
   row t's in-row stages lands in its own slot, and the positions the passes
   read hold the entries Algorithm 6 / 7 index (Psi_br[2^s + t 2^r + i]);
-* the odd slices' evens-first order makes the pair reads of the
-  block-fastest passes conflict-free.
+* the bulk copies (TMA) that stage those slices for 64-bit words: each slice
+  is one contiguous run of the table, both ends 16-byte aligned, the copies
+  tile slots 0 .. 1022 exactly and leave slot 1023 (the mbarrier) alone.
 """
 
 
@@ -69,17 +70,23 @@ def test_latency_rows_64bit():
 
 
 def _stage(LR, logn, t):
-    """Slot -> global table index of row t's staged slices (w_stage_tw)."""
+    """Slot -> global table index of row t's staged slices (w_stage_tw): slot
+    i = 2^r - 1 + e holds entry e of slice r."""
     slots = {}
     for i in range((1 << LR) - 1):
         r = (i + 1).bit_length() - 1
         e = i + 1 - (1 << r)
         idx = (1 << (logn - LR + r)) + (t << r) + e
-        pos = (((e & 1) << (r - 1)) + (e >> 1)) if (r & 1) else e
-        slot = (1 << r) - 1 + pos
+        slot = (1 << r) - 1 + e
         assert slot not in slots
         slots[slot] = idx
     return slots
+
+
+def _bulk(LR, logn, t):
+    """(smem slot, global index, entries) of each bulk copy of one table
+    (w_stage_tw_bulk): slice r, 2^r entries."""
+    return [((1 << r) - 1, (1 << (logn - LR + r)) + (t << r), 1 << r) for r in range(LR)]
 
 
 def test_twiddle_slices_hold_the_indexed_entries():
@@ -98,24 +105,23 @@ def test_twiddle_slices_hold_the_indexed_entries():
                     s0 = logn - LR + 2 * p
                     assert slots[(1 << (2 * p)) - 1 + blk] == (1 << s0) + (t << (2 * p)) + blk
                     # stage 2p+1, pair u/2 = 0, 1: entries 2 blk, 2 blk + 1
-                    base = (1 << (2 * p + 1)) - 1 + blk
-                    for h, slot in enumerate((base, base + (1 << (2 * p)))):
+                    base = (1 << (2 * p + 1)) - 1 + 2 * blk
+                    for h, slot in enumerate((base, base + 1)):
                         want = (1 << (s0 + 1)) + (t << (2 * p + 1)) + 2 * blk + h
                         assert slots[slot] == want, (logn, t, p, th, h)
 
 
-def test_odd_slice_pair_reads_are_conflict_free():
-    # 16-byte entries for 64-bit words: 8 threads per wavefront, 128 bytes
-    LR = 10
-    for p in range(LR // 2):
-        E = LR - 2 - 2 * p
-        if E >= 4:
-            continue  # offset-fastest passes: a half-warp shares blk (broadcast)
-        base = (1 << (2 * p + 1)) - 1
-        for h in (0, 1 << (2 * p)):
-            for q in range(0, 256, 8):
-                banks = []
-                for th in range(q, q + 8):
-                    _, blk = _geo(LR, E, th, 4)
-                    banks.append(((base + h + blk) * 16 // 4) % 32 // 4)
-                assert len(set(banks)) == 8, (p, h, q)
+def test_bulk_copies_match_the_staged_slices():
+    LR, TW = 10, 16  # 16-byte twiddle pairs (64-bit words)
+    for logn in (10, 13, 16, 17):
+        for t in sorted({0, 1, (1 << (logn - LR)) - 1} & set(range(1 << (logn - LR)))):
+            slots = _stage(LR, logn, t)
+            covered = []
+            for slot, idx, cnt in _bulk(LR, logn, t):
+                assert (slot * TW) % 16 == 0 and (idx * TW) % 16 == 0 and (cnt * TW) % 16 == 0
+                for e in range(cnt):
+                    assert slots[slot + e] == idx + e
+                covered += range(slot, slot + cnt)
+            assert sorted(covered) == list(range((1 << LR) - 1))
+            assert (1 << LR) - 1 not in covered  # the mbarrier's slot
+            assert sum(c for *_, c in _bulk(LR, logn, t)) * TW == ((1 << LR) - 1) * TW
