@@ -309,6 +309,11 @@ typedef struct pm_server_config {
 typedef struct pm_server_stats {
     uint64_t submitted, completed, batches, batched_requests, max_batch;
     uint64_t arena_peak_bytes, arena_used_bytes;
+    /* batches launched while others were still unretired, at most (host view) */
+    uint64_t max_inflight;
+    /* the largest number of batches whose device intervals (a timing event
+     * before and after each launch on its slot's stream) overlapped */
+    uint64_t max_device_overlap;
 } pm_server_stats;
 
 pm_status pm_server_create(pm_server **out, int device, const pm_server_config *cfg);
@@ -341,9 +346,14 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  *                           row tasks of all units from a work queue in a
  *                           software-pipelined order (lag_fwd / lag_inv are
  *                           the pipeline distances in units, ctas_per_sm the
- *                           resident CTAs per SM).  Uses a control block of
- *                           16 + 8 * units bytes in the stream's scratch.
- * row_ops (SPLIT only):
+ *                           resident CTAs per SM, 1..4, capped at what the
+ *                           kernel holds: 4 for the 1024-word tasks up to
+ *                           N = 2^16, else 3).  The tasks are those of the
+ *                           1024-word split (row_ops 0 or 4, no per-stage
+ *                           halving, N >= 2^13) or of 4096-word rows.  Uses
+ *                           a control block of 16 + 8 * units bytes in the
+ *                           stream's scratch.
+ * row_ops (SPLIT; for PERSISTENT the task size as above):
  *   1..3: the transform as rows of 4096 words (N >= 4096):
  *   1 = 256 threads per row, a transformed before b (3 CTAs per SM);
  *   2 = 256 threads per row, a and b together sharing twiddle loads

@@ -19,8 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpm_gb300.so")
-SOURCES = ["pm_kernels.cu", "pm_wide.cu", "pm_persist.cu", "pm_capi.cu", "pm_params.cpp",
-           "pm_microbench.cu", "pm_reduce.cu"]
+SOURCES = ["pm_kernels.cu", "pm_wide.cu", "pm_persist.cu", "pm_wpersist.cu", "pm_capi.cu",
+           "pm_params.cpp", "pm_microbench.cu", "pm_reduce.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                 "-diag-suppress", "128", "-I", INCLUDE]

@@ -251,7 +251,7 @@ class PmTuning(ctypes.Structure):
                 "lag_inv": self.lag_inv, "row_ops": self.row_ops}
 
 
-def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 3, lag_fwd: int = 8,
+def pm_plan_tune(plan: int, variant: int, ctas_per_sm: int = 4, lag_fwd: int = 8,
                  lag_inv: int = 64, row_ops: int = 0) -> None:
     t = PmTuning(variant, ctas_per_sm, lag_fwd, lag_inv, row_ops)
     _call("pm_plan_tune", plan, ctypes.byref(t))
@@ -374,7 +374,7 @@ class PmServerConfig(ctypes.Structure):
 class PmServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("submitted", "completed", "batches", "batched_requests", "max_batch",
-                 "arena_peak_bytes", "arena_used_bytes")]
+                 "arena_peak_bytes", "arena_used_bytes", "max_inflight", "max_device_overlap")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -253,6 +253,20 @@ bool use_persistent(const pm_plan* p) {
   return p->tune.variant == PM_VARIANT_PERSISTENT && p->logn >= 13 && !is_word32(p);
 }
 
+// One persistent launch with the plan's tuning: the 1024-word tasks (row
+// kernel choice 4, 1/N folded, N >= 2^13) or the 4096-word ones.
+cudaError_t launch_persistent(const pm_plan* p, const pm::KParams& P, uint32_t* ctl,
+                              cudaStream_t st, uint32_t withheld) {
+  if (P.row_ops == 4 && !P.halving && pm::wpersist_ok(p->logn)) {
+    const int ctas = std::min((int)p->tune.ctas_per_sm, pm::wpersist_ctas_per_sm(p->logn));
+    return pm::launch_polymul_wpersistent(P, ctl, p->num_sms * ctas, p->tune.lag_fwd,
+                                          p->tune.lag_inv, st, withheld);
+  }
+  const int ctas = std::min((int)p->tune.ctas_per_sm, 3);
+  return pm::launch_polymul_persistent(P, ctl, p->num_sms * ctas, p->tune.lag_fwd,
+                                       p->tune.lag_inv, st, withheld);
+}
+
 pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uint64_t* d_c,
                        uint32_t npoly, cudaStream_t st) {
   pm::KParams P = base_params(p, npoly);
@@ -269,8 +283,7 @@ pm_status polymul_impl(pm_plan* p, const uint64_t* d_a, const uint64_t* d_b, uin
       return cuda_fail(e, "event");
     const uint32_t withheld = (p->inject == PM_FAULT_WITHHOLD_SIGNAL) ? 1u : 0u;
     p->inject = 0;
-    e = pm::launch_polymul_persistent(P, ctl, p->num_sms * (int)p->tune.ctas_per_sm,
-                                      p->tune.lag_fwd, p->tune.lag_inv, st, withheld);
+    e = launch_persistent(p, P, ctl, st, withheld);
     if (e != cudaSuccess) return cuda_fail(e, "persistent polymul launch");
     for (int k = 1; pe && k < pe->n; ++k)
       if ((e = cudaEventRecord(pe->ev[k], st)) != cudaSuccess) return cuda_fail(e, "event");
@@ -392,6 +405,7 @@ pm_status pm_plan_create_ex(pm_plan** out, uint32_t log2n, uint32_t nlimbs, cons
   }
   e = prepare_device(device);
   if (e == cudaSuccess) e = pm::persist_prepare();
+  if (e == cudaSuccess) e = pm::wpersist_prepare();
   if (e != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e, "kernel attributes");
@@ -869,9 +883,9 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (t->variant == PM_VARIANT_PERSISTENT && is_word32(plan))
     return fail(PM_ERR_ARG, "the persistent variant takes 64-bit plans");
   if (t->variant == PM_VARIANT_PERSISTENT &&
-      (t->ctas_per_sm < 1 || t->ctas_per_sm > 3 || t->lag_fwd < 1 || t->lag_inv <= t->lag_fwd ||
+      (t->ctas_per_sm < 1 || t->ctas_per_sm > 4 || t->lag_fwd < 1 || t->lag_inv <= t->lag_fwd ||
        t->lag_inv > 4096))
-    return fail(PM_ERR_ARG, "persistent tuning needs 1 <= ctas_per_sm <= 3, 1 <= lag_fwd < lag_inv <= 4096");
+    return fail(PM_ERR_ARG, "persistent tuning needs 1 <= ctas_per_sm <= 4, 1 <= lag_fwd < lag_inv <= 4096");
   std::lock_guard<std::mutex> lk(plan->mu);
   plan->tune = *t;
   return ok();
@@ -898,6 +912,10 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
   if (plan->logn >= 13 && !is_word32(plan)) {
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});
+    if (pm::wpersist_ok(plan->logn) && !(plan->flags & PM_PLAN_HALVING)) {
+      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 2, 16, 4});
+      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 8, 64, 4});
+    }
   }
   const size_t words = (size_t)npoly * plan->nlimbs << plan->logn;
   uint64_t *a = nullptr, *b = nullptr, *c = nullptr;
@@ -1090,7 +1108,8 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     lazy16 = lazy16 && J.plan->lazy16;
     const uint64_t u = (uint64_t)J.npoly * J.plan->nlimbs;
     units += u;
-    if (J.plan->logn > 12 && J.a != J.b && !(ext_scratch && ext_scratch[j]))
+    // N = 2^12 units need b's image too on the 1024-word persistent path
+    if (J.plan->logn >= 12 && J.a != J.b && !(ext_scratch && ext_scratch[j]))
       scratch += u << J.plan->logn;
   }
   if (units > 0x3fffffffull) return fail(PM_ERR_ARG, "too many units (%llu)", (unsigned long long)units);
@@ -1116,6 +1135,9 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       rows_total += ((uint64_t)jobs[j].npoly * jobs[j].plan->nlimbs) << (jobs[j].plan->logn - 12);
   const bool grouped = q->mode == PM_UNEVEN_GROUPED ||
                        (q->mode == PM_UNEVEN_AUTO && rows_total >= kGroupedMinRows * (uint64_t)q->num_sms);
+  // one persistent launch: the 1024-word tasks unless the plans halve at
+  // every inverse stage (then the 4096-word tasks)
+  const bool wide = !grouped && halving != 1;
   if (q->staged_used && (e = cudaEventSynchronize(q->staged)) != cudaSuccess)
     return cuda_fail(e, "queue staging");
   // unit descriptors and section prefix counts
@@ -1130,7 +1152,7 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     const pm_plan* p = J.plan;
     if (p->logn < 12) continue;
     const uint64_t n = (uint64_t)1 << p->logn;
-    const bool split = p->logn > 12;
+    const bool split = p->logn > 12 || wide;
     const bool square = J.a == J.b;
     uint64_t* own = (ext_scratch && ext_scratch[j]) ? ext_scratch[j] : nullptr;
     for (uint32_t k = 0; k < J.npoly * p->nlimbs; ++k, ++u) {
@@ -1158,9 +1180,17 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
       pf[u] = tf;
       pw[u] = tw;
       pi[u] = ti;
-      tf += split ? (square ? 1u : 2u) * 16u : 0u;
-      tw += (uint32_t)(n >> 12);
-      ti += split ? 16u : 0u;
+      if (wide) {
+        uint32_t f, w, i;
+        pm::wuneven_tasks(p->logn, square, &f, &w, &i);
+        tf += f;
+        tw += w;
+        ti += i;
+      } else {
+        tf += split ? (square ? 1u : 2u) * 16u : 0u;
+        tw += (uint32_t)(n >> 12);
+        ti += split ? 16u : 0u;
+      }
     }
   }
   if (grouped) {
@@ -1215,8 +1245,11 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   A.tf = tf;
   A.tw = tw;
   A.ti = ti;
-  if ((e = pm::launch_uneven(A, halving == 1, fused == 1, q->num_sms * 3, st)) != cudaSuccess)
-    return cuda_fail(e, "uneven launch");
+  if (wide)
+    e = pm::launch_wuneven(A, lazy16, fused == 1, q->num_sms * pm::wpersist_ctas_per_sm(0), st);
+  else
+    e = pm::launch_uneven(A, halving == 1, fused == 1, q->num_sms * 3, st);
+  if (e != cudaSuccess) return cuda_fail(e, "uneven launch");
   return ok();
 }
 
@@ -1238,7 +1271,7 @@ pm_status pm_queue_create(pm_queue** out, int device) {
   if ((e = cudaDeviceGetAttribute(&q->num_sms, cudaDevAttrMultiProcessorCount, device)) !=
           cudaSuccess ||
       (e = prepare_device(device)) != cudaSuccess || (e = pm::persist_prepare()) != cudaSuccess ||
-      (e = pm::uneven_prepare()) != cudaSuccess ||
+      (e = pm::uneven_prepare()) != cudaSuccess || (e = pm::wpersist_prepare()) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&q->staged, cudaEventDisableTiming)) != cudaSuccess) {
     destroy_queue(q);
     return cuda_fail(e, "queue setup");
@@ -1361,10 +1394,8 @@ pm_status pm_graph_create_polymul(pm_graph** out, const pm_plan* plan, const uin
   }
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t le = persistent ? pm::launch_polymul_persistent(
-                                      P, g->ctl, plan->num_sms * (int)plan->tune.ctas_per_sm,
-                                      plan->tune.lag_fwd, plan->tune.lag_inv, cap)
-                                : pm::launch_polymul(P, cap);
+    cudaError_t le =
+        persistent ? launch_persistent(plan, P, g->ctl, cap, 0) : pm::launch_polymul(P, cap);
     e = cudaStreamEndCapture(cap, &g->graph);
     if (le != cudaSuccess) e = le;
   }
@@ -1472,7 +1503,7 @@ struct Request {
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;  // timing events around each launch
   pm_queue* queue = nullptr;
   bool busy = false;
   std::vector<uint64_t> ids;
@@ -1496,6 +1527,8 @@ struct pm_server {
   uint64_t queued_rows = 0;   // row tasks (4096-word rows) of the queued requests
   uint64_t min_rows = 0;      // launch threshold while another batch runs
   pm_server_stats stats{};
+  cudaEvent_t t0 = nullptr;  // time origin of the batches' device intervals
+  std::deque<std::pair<float, float>> recent;  // device intervals (ms) of the last batches
   pm_status worker_status = PM_OK;
   char worker_msg[256] = "";
 };
@@ -1503,7 +1536,8 @@ struct pm_server {
 namespace {
 
 uint64_t request_scratch_bytes(const pm_plan* p, uint32_t npoly, bool square) {
-  if (p->logn < 13 || square) return 0;
+  // N >= 2^12 (the 1024-word split keeps b's column image for N = 2^12 too)
+  if (p->logn < 12 || square) return 0;
   return (uint64_t)npoly * p->nlimbs << p->logn << 3;
 }
 
@@ -1532,6 +1566,16 @@ void server_loop(pm_server* S) {
         if (sl.queue->d_ctl && cudaMemcpy(&flag, sl.queue->d_ctl + 1, 4, cudaMemcpyDeviceToHost) == cudaSuccess && flag) {
           st = PM_ERR_TIMEOUT;
           cudaMemset(sl.queue->d_ctl + 1, 0, 4);
+        }
+        // the batch's device interval; count the recent batches it overlapped
+        float b0 = 0.f, b1 = 0.f;
+        if (cudaEventElapsedTime(&b0, S->t0, sl.start) == cudaSuccess &&
+            cudaEventElapsedTime(&b1, S->t0, sl.done) == cudaSuccess) {
+          uint64_t over = 1;
+          for (const auto& iv : S->recent) over += (iv.first < b1 && b0 < iv.second) ? 1 : 0;
+          if (over > S->stats.max_device_overlap) S->stats.max_device_overlap = over;
+          S->recent.emplace_back(b0, b1);
+          if (S->recent.size() > 64) S->recent.pop_front();
         }
       }
       for (uint64_t id : sl.ids) {
@@ -1594,8 +1638,9 @@ void server_loop(pm_server* S) {
         ids.push_back(id);
       }
       if (!ids.empty()) {
-        pm_status st;
-        {
+        pm_status st = PM_OK;
+        if (cudaEventRecord(free_slot->start, free_slot->stream) != cudaSuccess) st = PM_ERR_CUDA;
+        if (st == PM_OK) {
           std::lock_guard<std::mutex> lq(free_slot->queue->mu);
           st = uneven_impl(free_slot->queue, jobs.data(), (uint32_t)jobs.size(), scr.data(),
                            free_slot->stream);
@@ -1617,6 +1662,9 @@ void server_loop(pm_server* S) {
         } else {
           free_slot->ids = ids;
           free_slot->busy = true;
+          uint64_t busy = 0;
+          for (auto& sl : S->slots) busy += sl.busy ? 1 : 0;
+          if (busy > S->stats.max_inflight) S->stats.max_inflight = busy;
           S->stats.batches++;
           S->stats.batched_requests += ids.size();
           if (ids.size() > S->stats.max_batch) S->stats.max_batch = ids.size();
@@ -1649,10 +1697,12 @@ void destroy_server(pm_server* S) {
   }
   DeviceGuard g(S->device);
   for (auto& sl : S->slots) {
+    if (sl.start) cudaEventDestroy(sl.start);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.stream) cudaStreamDestroy(sl.stream);
     destroy_queue(sl.queue);
   }
+  if (S->t0) cudaEventDestroy(S->t0);
   cudaFree(S->arena_base);
   delete S;
 }
@@ -1692,10 +1742,18 @@ pm_status pm_server_create(pm_server** out, int device, const pm_server_config* 
       return st;
     }
     if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess) {
+        (e = cudaEventCreate(&sl.start)) != cudaSuccess ||
+        (e = cudaEventCreate(&sl.done)) != cudaSuccess) {
       destroy_server(S);
       return cuda_fail(e, "serving streams");
     }
+  }
+  // the time origin: recorded (and complete) before any batch is launched
+  if ((e = cudaEventCreate(&S->t0)) != cudaSuccess ||
+      (e = cudaEventRecord(S->t0, S->slots[0].stream)) != cudaSuccess ||
+      (e = cudaEventSynchronize(S->t0)) != cudaSuccess) {
+    destroy_server(S);
+    return cuda_fail(e, "serving time origin");
   }
   S->worker = std::thread(server_loop, S);
   *out = S;

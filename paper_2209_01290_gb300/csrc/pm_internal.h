@@ -91,6 +91,21 @@ size_t persist_ctl_words(uint32_t nunits);
 cudaError_t launch_polymul_persistent(const KParams& P, uint32_t* ctl, int grid, uint32_t lagF,
                                       uint32_t lagI, cudaStream_t st, uint32_t withheld = 0);
 
+// Persistent launches over the 1024-word split (pm_wpersist.cu): 64-bit
+// words, 1/N folded (no per-stage halving).
+bool wpersist_ok(uint32_t logn);  // uniform batches: N = 2^13 .. 2^17
+// resident CTAs per SM the kernel for N = 2^logn is built for (logn 0: the
+// uneven kernel)
+int wpersist_ctas_per_sm(uint32_t logn);
+// Tasks of one uneven unit of N = 2^logn (2^12 .. 2^17): column-forward,
+// row and column-inverse; returns their sum.
+uint32_t wuneven_tasks(uint32_t logn, bool square, uint32_t* f, uint32_t* w, uint32_t* i);
+cudaError_t wpersist_prepare();
+cudaError_t launch_polymul_wpersistent(const KParams& P, uint32_t* ctl, int grid, uint32_t lagF,
+                                       uint32_t lagI, cudaStream_t st, uint32_t withheld = 0);
+cudaError_t launch_wuneven(const UnevenArgs& A, bool lazy16, bool fused, int grid,
+                           cudaStream_t st);
+
 cudaError_t kernels_prepare();
 cudaError_t launch_polymul(const KParams& P, cudaStream_t st,
                            const PhaseEvents* pe = nullptr);

@@ -469,32 +469,38 @@ __device__ __forceinline__ bool w_row_task(const KParams& P, uint32_t unit, uint
 }
 
 // Column shape for CL column stages (R = 2^CL words per column).
-// TH threads work on CT = TH / J columns (a column-task tile).
-template <int CL, int TH = kWColThreads>
+// TH threads work on CT = TH / J columns (a column-task tile), at most MW
+// words per thread: a column of R > MW words is shared by J = R / MW
+// threads, which needs R <= MW^2 (the stages after the transpose pair words
+// of one thread's group).
+template <int CL, int TH = kWColThreads, int MW = 16>
 struct WCol {
   static constexpr int R = 1 << CL;
-  static constexpr int J = CL > 4 ? 1 << (CL - 4) : 1;  // threads per column
+  static constexpr int J = R > MW ? R / MW : 1;          // threads per column
   static constexpr int M = R / J;                        // words per thread
   static constexpr int CT = TH / J;                      // columns per tile
   static constexpr int kTiles = kW / CT;                 // tiles per unit and operand
   static constexpr int kSmemWords = J > 1 ? R * CT : 1;  // transpose buffer
+  static_assert(J <= M, "column too long for MW words per thread");
 };
 
-// Forward column stages 4 .. 4 + log2 G - 1 on the 16/G groups of G
-// consecutive column words held in x (group m is block g0 + m at stage 4):
-// stage 4 + D pairs words G/2^(D+1) apart with twiddle
-// Psi_br[2^(4+D) + (g0 + m) 2^D + b] for block b of the group.
-template <int G, int D, bool RED, typename W>
-__device__ __forceinline__ void ct_tail(W (&x)[16], const typename WordT<W>::Tw* __restrict__ tw,
+// Forward column stages LM .. LM + log2 G - 1 (LM = log2 M) on the M/G
+// groups of G consecutive column words held in x (group m is block g0 + m at
+// stage LM): stage LM + D pairs words G/2^(D+1) apart with twiddle
+// Psi_br[2^(LM+D) + (g0 + m) 2^D + b] for block b of the group.
+template <int G, int D, bool RED, typename W, int M>
+__device__ __forceinline__ void ct_tail(W (&x)[M], const typename WordT<W>::Tw* __restrict__ tw,
                                         uint32_t g0, W q, W two_q) {
+  constexpr int LM = M == 16 ? 4 : M == 8 ? 3 : M == 4 ? 2 : M == 2 ? 1 : 0;
+  static_assert((1 << LM) == M, "M is a power of two up to 16");
   if constexpr ((1 << D) < G) {
     constexpr int h = G >> (D + 1);
     constexpr int nb = 1 << D;
 #pragma unroll
-    for (int m = 0; m < 16 / G; m++)
+    for (int m = 0; m < M / G; m++)
 #pragma unroll
       for (int b = 0; b < nb; b++) {
-        const auto w = ld_tw(tw + (1u << (4 + D)) + ((g0 + m) << D) + b);
+        const auto w = ld_tw(tw + (1u << (LM + D)) + ((g0 + m) << D) + b);
 #pragma unroll
         for (int u0 = 0; u0 < h; u0++)
           ct_bfly_m<RED>(x[G * m + 2 * h * b + u0], x[G * m + 2 * h * b + u0 + h], w.w, w.wp, q,
@@ -505,21 +511,21 @@ __device__ __forceinline__ void ct_tail(W (&x)[16], const typename WordT<W>::Tw*
 }
 
 // Inverse column stages with word distance 2^D < G (the first log2 G column
-// stages of Algorithm 7 after the 10 in-row ones) on the groups of G
+// stages of Algorithm 7 after the 10 in-row ones) on the M/G groups of G
 // consecutive words held in x (group m = column words G (g0 + m) ...): the
 // pair (t, t + 2^D) takes Psi^-1_br[(R >> (D+1)) + (t >> (D+1))] with
-// R = 16 G.
-template <int G, int D, bool HALVE, bool LZ, typename W>
-__device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw* __restrict__ tw,
+// R = M G.
+template <int G, int D, bool HALVE, bool LZ, typename W, int M>
+__device__ __forceinline__ void gs_tail(W (&x)[M], const typename WordT<W>::Tw* __restrict__ tw,
                                         uint32_t g0, const typename WordT<W>::LC& K) {
   if constexpr ((1 << D) < G) {
     constexpr int h = 1 << D;
     constexpr int nb = G / (2 * h);
 #pragma unroll
-    for (int m = 0; m < 16 / G; m++)
+    for (int m = 0; m < M / G; m++)
 #pragma unroll
       for (int b = 0; b < nb; b++) {
-        const uint32_t idx = ((16u * G) >> (D + 1)) + (g0 + m) * (uint32_t)nb + b;
+        const uint32_t idx = (((uint32_t)M * G) >> (D + 1)) + (g0 + m) * (uint32_t)nb + b;
         const auto w = ld_tw(tw + idx);
 #pragma unroll
         for (int u0 = 0; u0 < h; u0++) {
@@ -543,10 +549,10 @@ __device__ __forceinline__ void gs_tail(W (&x)[16], const typename WordT<W>::Tw*
 // stages: images below (1 + 2 CL) q <= 15q).
 // Column-forward task: columns [tile CT, (tile+1) CT) of operand op of
 // `unit`, TH threads; tile_s: R CT words of shared memory (J > 1 only).
-template <int CL, typename W, bool DESC, bool LZ, int TH = kWColThreads>
+template <int CL, typename W, bool DESC, bool LZ, int TH = kWColThreads, int MW = 16>
 __device__ __forceinline__ void w_colf_task(const KParams& P, uint32_t unit, uint32_t op,
                                             uint32_t tile, W* tile_s) {
-  using S = WCol<CL, TH>;
+  using S = WCol<CL, TH, MW>;
   const WUnit<W, DESC> U(P, unit);
   if (DESC && op == 1 && U.a == U.b) return;  // a square: one image, read twice
   const int th = threadIdx.x;
@@ -579,10 +585,11 @@ __device__ __forceinline__ void w_colf_task(const KParams& P, uint32_t unit, uin
 // output [0, 2q) in, canonical words out.
 // LZ: wide lazy ranges (rows' output below 8q; every sum reduced by 8q).
 // Column-inverse task: columns [tile CT, (tile+1) CT) of `unit`, TH threads.
-template <int CL, bool HALVE, typename W, bool DESC, bool LZ, int TH = kWColThreads>
+template <int CL, bool HALVE, typename W, bool DESC, bool LZ, int TH = kWColThreads,
+          int MW = 16>
 __device__ __forceinline__ void w_coli_task(const KParams& P, uint32_t unit, uint32_t tile,
                                             W* tile_s) {
-  using S = WCol<CL, TH>;
+  using S = WCol<CL, TH, MW>;
   const WUnit<W, DESC> U(P, unit);
   const int th = threadIdx.x;
   const int c = th % S::CT, j = th / S::CT;

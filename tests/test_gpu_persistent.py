@@ -20,15 +20,18 @@ def _setup(log2n, L, P, seed):
 
 @pytest.mark.parametrize("log2n,L,P", [(13, 4, 16), (14, 3, 8), (15, 2, 8), (16, 4, 6), (17, 2, 3)])
 @pytest.mark.parametrize("lags", [(1, 2), (8, 16), (40, 90)])
-def test_persistent_lags(oracle, log2n, L, P, lags):
-    """Results do not depend on the pipeline distances or on the CTA count;
+@pytest.mark.parametrize("row_ops", [0, 1], ids=["rows1024", "rows4096"])
+def test_persistent_lags(oracle, log2n, L, P, lags, row_ops):
+    """Results do not depend on the pipeline distances, on the CTA count or
+    on the task size (1024-word split, the default, or 4096-word rows);
     every unit is checked against the oracle (units > lag exercise the
     steady state, units < lag the prologue/epilogue)."""
     from paper_2209_01290_gb300 import capi
     plan, qs, psis, a, b = _setup(log2n, L, P, 11000 + log2n)
     want = oracle_polymul_batch(oracle, a, b, qs, psis)
-    for ctas in (1, 3):
-        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT, ctas, lags[0], lags[1])
+    for ctas in (1, 4):
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT, ctas, lags[0], lags[1],
+                          row_ops=row_ops)
         got = to_host(plan.polymul(to_dev(a), to_dev(b)))
         plan.sync()
         assert np.array_equal(got, want), (ctas, lags)
@@ -40,7 +43,7 @@ def test_tuning_validation():
     t = capi.pm_plan_get_tuning(plan.handle)
     assert t.variant == capi.PM_VARIANT_SPLIT and t.ctas_per_sm == 3 and t.row_ops == 0
     for bad in [(capi.PM_VARIANT_PERSISTENT, 0, 8, 16), (capi.PM_VARIANT_PERSISTENT, 3, 8, 8),
-                (capi.PM_VARIANT_PERSISTENT, 4, 8, 16), (7, 3, 8, 16)]:
+                (capi.PM_VARIANT_PERSISTENT, 5, 8, 16), (7, 3, 8, 16)]:
         with pytest.raises(capi.PMError) as e:
             capi.pm_plan_tune(plan.handle, *bad)
         assert e.value.status == -1

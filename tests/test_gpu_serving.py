@@ -27,6 +27,13 @@ def _copy_out(ptr, shape):
 
 @pytest.mark.parametrize("budget_mb,inflight", [(2048, 2), (24, 2), (24, 1)])
 def test_server_mix_equals_alone(oracle, budget_mb, inflight):
+    """40 requests of mixed N (2^10 .. 2^16), limb counts and batch sizes
+    (some squares), submitted from another thread.  Every result equals the
+    product computed alone and the oracle's product.  The 24 MiB budget makes
+    requests wait for admission while others run.  With two slots and no
+    launch threshold (min_batch_rows 1) the device intervals of at least two
+    batches overlap (timing events around each launch); with one slot they
+    never do."""
     import torch
     from paper_2209_01290_gb300 import Plan, capi
     shapes = [(13, 3), (15, 1), (16, 2), (12, 4), (10, 2), (16, 1), (14, 2)]
@@ -37,31 +44,36 @@ def test_server_mix_equals_alone(oracle, budget_mb, inflight):
     rng = np.random.default_rng(budget_mb + inflight)
     reqs = []
     for i in range(40):
-        log2n, L = shapes[int(rng.integers(len(shapes)))]
+        # a heavy request first: it is still on the device when the next
+        # batch launches
+        log2n, L = (16, 2) if i == 0 else shapes[int(rng.integers(len(shapes)))]
         plan, qs, psis = plans[(log2n, L)]
-        P = int(rng.integers(1, 3))
+        P = 4 if i == 0 else int(rng.integers(1, 3))
         a, b = operands(30000 + i, qs, P, 1 << log2n)
-        da, db = to_dev(a), to_dev(b)
         if i % 7 == 3:
-            db = da  # a square
+            b = a  # a square
+        da = to_dev(a)
+        db = da if i % 7 == 3 else to_dev(b)
         alone = plan.polymul(da, db)
-        reqs.append((plan, da, db, P, alone))
+        reqs.append((plan, da, db, P, alone, a, b, qs, psis))
     torch.cuda.synchronize()
-    srv = capi.pm_server_create(0, budget_mb << 20, 0, inflight)
+    srv = capi.pm_server_create(0, budget_mb << 20, 0, inflight, min_batch_rows=1)
     ids = [None] * len(reqs)
 
     def producer():
-        for i, (plan, da, db, P, _) in enumerate(reqs):
+        for i, (plan, da, db, P, *_rest) in enumerate(reqs):
             ids[i] = capi.pm_server_submit(srv, plan.handle, da.data_ptr(), db.data_ptr(), P)
 
     th = threading.Thread(target=producer)
     th.start()
     th.join()
-    for i, (plan, da, db, P, alone) in enumerate(reqs):
+    outs = []
+    for i, (plan, da, db, P, alone, *_rest) in enumerate(reqs):
         ptr, lat = capi.pm_server_wait(srv, ids[i])
         assert lat > 0
         got = _copy_out(ptr, alone.shape)
         assert torch.equal(got, alone), i
+        outs.append(to_host(got))
         capi.pm_server_release(srv, ids[i])
     st = capi.pm_server_get_stats(srv)
     assert st["submitted"] == st["completed"] == len(reqs)
@@ -69,12 +81,16 @@ def test_server_mix_equals_alone(oracle, budget_mb, inflight):
     assert st["arena_peak_bytes"] <= budget_mb << 20
     if budget_mb >= 2048:
         assert st["batches"] < len(reqs)  # requests were batched together
+    assert st["max_inflight"] <= inflight
+    if inflight >= 2:
+        assert st["max_device_overlap"] >= 2, st  # batches overlapped on the device
+    else:
+        assert st["max_device_overlap"] == 1, st
     capi.pm_server_destroy(srv)
-    # and the products themselves are right
-    plan, da, db, P, alone = reqs[0]
-    _, qs, psis = plans[(plan.log2n, plan.nlimbs)]
-    want = oracle_polymul_batch(oracle, to_host(da), to_host(db), qs, psis)
-    assert np.array_equal(to_host(alone), want)
+    # every result is the oracle's product
+    for i, (plan, da, db, P, alone, a, b, qs, psis) in enumerate(reqs):
+        want = oracle_polymul_batch(oracle, a, b, qs, psis)
+        assert np.array_equal(outs[i], want), i
 
 
 def test_server_budget_rejects_oversized():
