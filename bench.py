@@ -246,10 +246,10 @@ def run_gpu(args):
 
     peak_mulmod, peak_imad = capi.pm_measure_peaks(dev)
     if args.variant == "split":
-        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT)
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=args.row_ops)
     elif args.variant == "persistent":
         capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_PERSISTENT, args.ctas_per_sm,
-                          args.lag_fwd, args.lag_inv)
+                          args.lag_fwd, args.lag_inv, row_ops=args.row_ops)
     tuning = capi.pm_plan_get_tuning(plan.handle)
     persistent = tuning.variant == capi.PM_VARIANT_PERSISTENT and log2n >= 13
 
@@ -764,6 +764,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--ctas-per-sm", type=int, default=4)
+    ap.add_argument("--row-ops", type=int, default=0,
+                    help="launch choice with --variant split/persistent (pm_tuning.row_ops; "
+                         "5: tensor-copy column tiles)")
     ap.add_argument("--lag-fwd", type=int, default=8)
     ap.add_argument("--lag-inv", type=int, default=16)
     args = ap.parse_args()

@@ -157,7 +157,10 @@ pm::KParams base_params(const pm_plan* p, uint32_t npoly) {
   const bool wide = p->logn >= 10 && (is_word32(p) ? words <= (1ull << 20)
                                                    : !(p->logn == 12 && P.nunits > 64));
   const uint64_t row_ctas = p->logn >= 12 ? (uint64_t)P.nunits << (p->logn - 12) : 0;
-  P.row_ops = p->tune.row_ops ? p->tune.row_ops
+  // row_ops 5: the 1024-word split with tensor-copy column tiles
+  P.tma_cols = (p->tune.row_ops == 5 && !is_word32(p) && !(p->flags & PM_PLAN_HALVING)) ? 1 : 0;
+  P.row_ops = p->tune.row_ops == 5 ? 4u
+              : p->tune.row_ops ? p->tune.row_ops
               : wide          ? 4u
                               : (row_ctas <= (uint64_t)p->num_sms ? 3u : 2u);
   P.fused = (p->flags & PM_PLAN_FUSED) ? 1 : 0;  // read by the polymul launchers only
@@ -879,7 +882,7 @@ pm_status pm_plan_tune(pm_plan* plan, const pm_tuning* t) {
   if (!t) return fail(PM_ERR_ARG, "tuning is NULL");
   if (t->variant != PM_VARIANT_SPLIT && t->variant != PM_VARIANT_PERSISTENT)
     return fail(PM_ERR_ARG, "unknown variant %d", t->variant);
-  if (t->row_ops > 4) return fail(PM_ERR_ARG, "row_ops must be 0..4");
+  if (t->row_ops > 5) return fail(PM_ERR_ARG, "row_ops must be 0..5");
   if (t->variant == PM_VARIANT_PERSISTENT && is_word32(plan))
     return fail(PM_ERR_ARG, "the persistent variant takes 64-bit plans");
   if (t->variant == PM_VARIANT_PERSISTENT &&
@@ -1035,6 +1038,11 @@ void destroy_queue(pm_queue* q) {
   delete q;
 }
 
+// Words of the prefix buffer per unit of capacity: three prefix counts, then
+// the 1024-word kernel's block tables (one entry per 32 tickets of a
+// section: at most 224 tickets per unit, 7 entries, plus one per section).
+constexpr size_t kPreWords = 3 + 8;
+
 pm_status queue_reserve(pm_queue* q, size_t units, size_t scratch_words) {
   cudaError_t e;
   if (units > q->cap) {
@@ -1052,10 +1060,10 @@ pm_status queue_reserve(pm_queue* q, size_t units, size_t scratch_words) {
     q->cap = q->h_cap = 0;
     const size_t cap = units < 256 ? 256 : units;
     if ((e = cudaMalloc(&q->d_units, cap * sizeof(pm::UnitDesc))) != cudaSuccess ||
-        (e = cudaMalloc(&q->d_pre, 3 * cap * sizeof(uint32_t))) != cudaSuccess ||
+        (e = cudaMalloc(&q->d_pre, kPreWords * cap * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMalloc(&q->d_ctl, (4 + 2 * cap) * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMallocHost(&q->h_units, cap * sizeof(pm::UnitDesc))) != cudaSuccess ||
-        (e = cudaMallocHost(&q->h_pre, 3 * cap * sizeof(uint32_t))) != cudaSuccess)
+        (e = cudaMallocHost(&q->h_pre, kPreWords * cap * sizeof(uint32_t))) != cudaSuccess)
       return cuda_fail(e, "queue buffers");
     if ((e = cudaMemset(q->d_ctl, 0, (4 + 2 * cap) * sizeof(uint32_t))) != cudaSuccess)
       return cuda_fail(e, "queue ctl");
@@ -1227,10 +1235,29 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
     }
     return ok();
   }
-  // the three prefix arrays are uploaded contiguously, in the order f, w, i
+  // the 1024-word kernel's block tables: per section, the unit holding every
+  // 32nd ticket (all units have tickets in every section)
+  size_t nblk[3] = {0, 0, 0};
+  if (wide) {
+    const uint32_t* pres[3] = {pf, pw, pi};
+    const uint32_t tot[3] = {tf, tw, ti};
+    uint32_t* blk = q->h_pre + 3 * units;
+    for (int sec = 0; sec < 3; ++sec) {
+      nblk[sec] = (tot[sec] + 31) / 32;
+      size_t uu = 0;
+      for (size_t i = 0; i < nblk[sec]; ++i) {
+        const uint32_t x = (uint32_t)(32 * i);
+        while (uu + 1 < units && pres[sec][uu + 1] <= x) ++uu;
+        blk[i] = (uint32_t)uu;
+      }
+      blk += nblk[sec];
+    }
+  }
+  const size_t pre_words = 3 * units + nblk[0] + nblk[1] + nblk[2];
+  // the prefix arrays (f, w, i) and block tables are uploaded contiguously
   if ((e = cudaMemcpyAsync(q->d_units, q->h_units, units * sizeof(pm::UnitDesc),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(q->d_pre, q->h_pre, 3 * units * sizeof(uint32_t), cudaMemcpyHostToDevice,
+      (e = cudaMemcpyAsync(q->d_pre, q->h_pre, pre_words * sizeof(uint32_t), cudaMemcpyHostToDevice,
                            st)) != cudaSuccess ||
       (e = cudaEventRecord(q->staged, st)) != cudaSuccess)
     return cuda_fail(e, "queue upload");
@@ -1245,6 +1272,9 @@ pm_status uneven_impl(pm_queue* q, const pm_job* jobs, uint32_t njobs, uint64_t*
   A.tf = tf;
   A.tw = tw;
   A.ti = ti;
+  A.blk_f = q->d_pre + 3 * units;
+  A.blk_w = A.blk_f + nblk[0];
+  A.blk_i = A.blk_w + nblk[1];
   if (wide)
     e = pm::launch_wuneven(A, lazy16, fused == 1, q->num_sms * pm::wpersist_ctas_per_sm(0), st);
   else

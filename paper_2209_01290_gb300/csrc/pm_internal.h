@@ -39,7 +39,8 @@ struct KParams {
   int* err;              // device flag: set (to 1) by a CTA whose bounded wait for its
                          // staged twiddles gave up (NULL: not recorded)
   uint32_t inject_tx;    // test hook: extra bytes each row CTA's barrier expects (0)
-  uint32_t pad2;
+  uint32_t tma_cols;     // 1024-word split, 64-bit words, 1/N folded: the column kernels
+                         // load their tiles with 2-D tensor copies (pm_plan_tune row_ops 5)
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the
@@ -57,6 +58,13 @@ struct PersistArgs {
   uint32_t lagI;    // ticket groups between a unit's column-forward and column-inverse tasks
   uint32_t ntasks;  // total tickets
   uint32_t withheld;  // fault injection: row tasks wait for this many extra signals (0)
+  // Compact ticket order (1024-word persistent kernel): groups 0 .. nunits +
+  // lagI - 1 fall into nseg segments; segment k covers groups seg_g[k] ..
+  // seg_g[k+1] - 1, starts at ticket seg_t[k], and its groups hold the tasks
+  // the bits of seg_mask[k] name (1: column-forward, 2: rows, 4: column-
+  // inverse), so no ticket is empty.
+  uint32_t nseg;
+  uint32_t seg_g[8], seg_t[8], seg_mask[8];
 };
 
 // Uneven batch (pm_persist.cu): one descriptor per unit.
@@ -80,6 +88,12 @@ struct UnevenArgs {
   uint32_t* ctl;          // [0] ticket, [1] error flag, [4 + 2u] per-unit counters
   uint32_t nunits;
   uint32_t tf, tw, ti;    // tickets per section
+  // 1024-word uneven kernel: blk[k][i] = the unit holding ticket i * 32 of
+  // section k (section-relative), so a ticket's unit is found from there by
+  // a short forward scan of the prefix counts
+  const uint32_t* blk_f;
+  const uint32_t* blk_w;
+  const uint32_t* blk_i;
 };
 
 cudaError_t uneven_prepare();

@@ -53,6 +53,8 @@
 #include <climits>
 #include <cstdint>
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime)
+
 #include "pm_wide.cuh"
 
 namespace pm {
@@ -96,6 +98,139 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   const uint32_t unit = blockIdx.x / S::kTiles;
   if (unit >= P.nunits) return;
   w_coli_task<CL, HALVE, W, DESC, LZ>(P, unit, tile, tile_s);
+}
+
+// ------------------------------------------------- tensor-copy column tiles
+// The same column stages with the CTA's tile -- R rows x CT columns of the
+// unit's [R][1024] image -- loaded by one 2-D tensor copy (TMA) into shared
+// memory instead of 16 strided loads per thread; the inverse kernel also
+// writes its tile back with one 2-D tensor copy.  64-bit words, 1/N folded.
+// The tensor maps view an operand array as a 2-D tensor of nunits R rows of
+// 1024 words (row stride 8 KB) with a box of CT x R words; tile x of unit u
+// is the box at (x CT, u R).  The mbarrier wait is bounded like the row
+// kernel's (P.err on giving up).
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n\t"
+      "cp.async.bulk.commit_group;" ::"l"(map),
+      "r"(x), "r"(y), "r"(smem_u32(src))
+      : "memory");
+}
+
+// One thread: load the CTA's tile; every thread: wait for it (bounded).
+// Returns false (CTA-uniform) when the wait gave up.
+template <int BYTES>
+__device__ __forceinline__ bool tma_tile_in(uint64_t* tile, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar, const KParams& P) {
+  if (threadIdx.x == 0) {
+    mbar_init1(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(BYTES + P.inject_tx)
+                 : "memory");
+    tma_load_2d(tile, map, x, y, bar);
+  }
+  __syncthreads();
+  const bool done = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) {
+      if (P.err) atomicOr(P.err, 1);
+      mbar_wait_bounded(bar, 0);
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <int CL, bool LZ>
+__global__ void __launch_bounds__(kWColThreads) k_wcol_fwd_tma(KParams P, int nops,
+                                                               const __grid_constant__ CUtensorMap ma,
+                                                               const __grid_constant__ CUtensorMap mb) {
+  using W = uint64_t;
+  using S = WCol<CL>;
+  __shared__ __align__(128) W tile[S::R * S::CT];
+  __shared__ uint64_t bar;
+  const uint32_t t = blockIdx.x % S::kTiles;
+  const uint32_t rest = blockIdx.x / S::kTiles;
+  const uint32_t op = rest % (uint32_t)nops, unit = rest / (uint32_t)nops;
+  if (unit >= P.nunits) return;
+  if (!tma_tile_in<S::R * S::CT * 8>(tile, op == 0 ? &ma : &mb, (int)(t * S::CT),
+                                      (int)(unit * S::R), &bar, P))
+    return;
+  const WUnit<W, false> U(P, unit);
+  const int th = threadIdx.x;
+  const int c = th % S::CT, j = th / S::CT;
+  const auto& K = U.K;
+  W* dst = (op == 0 ? U.c : U.s) + t * S::CT + c;
+  W x[S::M];
+#pragma unroll
+  for (int k = 0; k < S::M; k++) x[k] = tile[(j + S::J * k) * S::CT + c];
+  ct_col<S::M, W, !LZ>(x, U.twf, K.q, K.two_q);
+  if constexpr (S::J > 1) {
+#pragma unroll
+    for (int k = 0; k < S::M; k++) tile[(j + S::J * k) * S::CT + c] = x[k];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::M; i++) x[i] = tile[(S::M * j + i) * S::CT + c];
+    ct_tail<S::J, 0, !LZ>(x, U.twf, (uint32_t)(S::M / S::J * j), K.q, K.two_q);
+#pragma unroll
+    for (int i = 0; i < S::M; i++) dst[(size_t)(S::M * j + i) * kW] = x[i];
+  } else {
+#pragma unroll
+    for (int k = 0; k < S::M; k++) dst[(size_t)k * kW] = x[k];
+  }
+}
+
+template <int CL, bool LZ>
+__global__ void __launch_bounds__(kWColThreads) k_wcol_inv_tma(KParams P,
+                                                               const __grid_constant__ CUtensorMap mc) {
+  using W = uint64_t;
+  using S = WCol<CL>;
+  __shared__ __align__(128) W tile[S::R * S::CT];
+  __shared__ uint64_t bar;
+  const uint32_t t = blockIdx.x % S::kTiles;
+  const uint32_t unit = blockIdx.x / S::kTiles;
+  if (unit >= P.nunits) return;
+  if (!tma_tile_in<S::R * S::CT * 8>(tile, &mc, (int)(t * S::CT), (int)(unit * S::R), &bar, P))
+    return;
+  const WUnit<W, false> U(P, unit);
+  const int th = threadIdx.x;
+  const int c = th % S::CT, j = th / S::CT;
+  const auto& K = U.K;
+  W x[S::M];
+  if constexpr (S::J > 1) {
+#pragma unroll
+    for (int i = 0; i < S::M; i++) x[i] = tile[(S::M * j + i) * S::CT + c];
+    gs_tail<S::J, 0, false, LZ>(x, U.twi, (uint32_t)(S::M / S::J * j), K);
+#pragma unroll
+    for (int i = 0; i < S::M; i++) tile[(S::M * j + i) * S::CT + c] = x[i];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S::M; k++) x[k] = tile[(j + S::J * k) * S::CT + c];
+  } else {
+#pragma unroll
+    for (int k = 0; k < S::M; k++) x[k] = tile[k * S::CT + c];
+  }
+  gs_col<S::M, false, W, LZ>(x, U.twi, K);
+  // the canonical words back into the tile, then one tensor copy to c
+  if constexpr (S::J > 1) __syncthreads();  // everyone has read the transposed words
+#pragma unroll
+  for (int k = 0; k < S::M; k++) tile[(j + S::J * k) * S::CT + c] = csub(x[k], K.q);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (th == 0) {
+    tma_store_2d(&mc, (int)(t * S::CT), (int)(unit * S::R), tile);
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // tile read before exit
+  }
 }
 
 // N = 2^(10+CL), CL = 1..3: one cluster of R = 2^CL CTAs per unit, CTA rank
@@ -222,8 +357,59 @@ cudaError_t wrows(const KParams& P, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// An operand array of nunits R rows of 1024 words as a 2-D tensor, box CT x R.
+cudaError_t col_map(CUtensorMap* m, const void* base, uint32_t nunits, int R, int CT) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {(cuuint64_t)kW, (cuuint64_t)nunits * (cuuint64_t)R};
+  const cuuint64_t strides[1] = {(cuuint64_t)kW * 8};
+  const cuuint32_t box[2] = {(cuuint32_t)CT, (cuuint32_t)R};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CL, typename W>
 cudaError_t wcol_fwd_cl(const KParams& P, int nops, cudaStream_t st) {
+  if constexpr (sizeof(W) == 8) {
+    if (P.tma_cols && !P.halving) {
+      using S = WCol<CL>;
+      CUtensorMap ma, mb;
+      cudaError_t e = col_map(&ma, P.a, P.nunits, S::R, S::CT);
+      if (e == cudaSuccess) e = col_map(&mb, nops > 1 ? P.b : P.a, P.nunits, S::R, S::CT);
+      if (e != cudaSuccess) return e;
+      const size_t blocks = (size_t)P.nunits * nops * S::kTiles;
+      if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
+      if (use_lazy16<W>(P))
+        k_wcol_fwd_tma<CL, true><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, nops, ma, mb);
+      else
+        k_wcol_fwd_tma<CL, false><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, nops, ma, mb);
+      return cudaGetLastError();
+    }
+  }
   const size_t blocks = (size_t)P.nunits * nops * WCol<CL>::kTiles;
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
   if (use_lazy16<W>(P))
@@ -235,6 +421,21 @@ cudaError_t wcol_fwd_cl(const KParams& P, int nops, cudaStream_t st) {
 
 template <int CL, typename W>
 cudaError_t wcol_inv_cl(const KParams& P, cudaStream_t st) {
+  if constexpr (sizeof(W) == 8) {
+    if (P.tma_cols && !P.halving) {
+      using S = WCol<CL>;
+      CUtensorMap mc;
+      cudaError_t e = col_map(&mc, P.c, P.nunits, S::R, S::CT);
+      if (e != cudaSuccess) return e;
+      const size_t blocks = (size_t)P.nunits * S::kTiles;
+      if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
+      if (use_lazy16<W>(P))
+        k_wcol_inv_tma<CL, true><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, mc);
+      else
+        k_wcol_inv_tma<CL, false><<<(unsigned)blocks, kWColThreads, 0, st>>>(P, mc);
+      return cudaGetLastError();
+    }
+  }
   const size_t blocks = (size_t)P.nunits * WCol<CL>::kTiles;
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
   if (use_lazy16<W>(P))

@@ -28,6 +28,7 @@
 // the CTA's mbarrier, one phase per row task.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "pm_internal.h"
@@ -68,38 +69,46 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<CL>) k_wpersist(KParams P, 
   if (threadIdx.x == 0) mbar_init1(w_row_bar<uint64_t>(smem));
   __syncthreads();
   uint32_t phase = 0;
-  const uint32_t GS = A.F + A.W + A.I;
   for (;;) {
     if (threadIdx.x == 0) s_ticket = atomicAdd(A.ctl, 1u);
     __syncthreads();
     const uint32_t ticket = s_ticket;
     __syncthreads();  // everyone has read s_ticket before thread 0 rewrites it
     if (ticket >= A.ntasks) break;
-    const uint32_t g = ticket / GS;
-    uint32_t r = ticket - g * GS;
+    // the ticket's segment, group and task within the group (no empty tickets)
+    uint32_t k = 0;
+    while (k + 1 < A.nseg && ticket >= A.seg_t[k + 1]) ++k;
+    const uint32_t mask = A.seg_mask[k];
+    const uint32_t gs = ((mask & 1) ? A.F : 0u) + ((mask & 2) ? A.W : 0u) + ((mask & 4) ? A.I : 0u);
+    const uint32_t off = ticket - A.seg_t[k];
+    const uint32_t g = A.seg_g[k] + off / gs;
+    uint32_t r = off % gs;
+    uint32_t kind = 0;  // 0: column forward, 1: row, 2: column inverse
+    if (!((mask & 1) && r < A.F)) {
+      if (mask & 1) r -= A.F;
+      if ((mask & 2) && r < A.W) {
+        kind = 1;
+      } else {
+        if (mask & 2) r -= A.W;
+        kind = 2;
+      }
+    }
     bool stop = false;
-    if (r < A.F) {  // ---- column forward, unit g
-      if (g < P.nunits) {
-        w_colf_task<CL, uint64_t, false, LZ, kWThreads, kWpMW<CL>>(P, g, r / S::kTiles,
-                                                                    r % S::kTiles, wp_tile(smem));
-        cta_signal(done + 2 * g);
-      }
-    } else if ((r -= A.F) < A.W) {  // ---- row r of unit g - lagF
-      if (g >= A.lagF && g - A.lagF < P.nunits) {
-        const uint32_t unit = g - A.lagF;
-        cta_wait(done + 2 * unit, A.F + A.withheld, err);
-        stop = !w_row_task<MODE, false, uint64_t, false, LZ>(P, unit, r, smem, phase);
-        phase ^= 1u;
-        cta_signal(done + 2 * unit + 1);
-      }
-    } else {  // ---- column inverse r - W of unit g - lagI
-      r -= A.W;
-      if (g >= A.lagI && g - A.lagI < P.nunits) {
-        const uint32_t unit = g - A.lagI;
-        cta_wait(done + 2 * unit + 1, A.W, err);
-        w_coli_task<CL, false, uint64_t, false, LZ, kWThreads, kWpMW<CL>>(P, unit, r,
-                                                                          wp_tile(smem));
-      }
+    if (kind == 0) {  // ---- column forward, unit g
+      w_colf_task<CL, uint64_t, false, LZ, kWThreads, kWpMW<CL>>(P, g, r / S::kTiles,
+                                                                  r % S::kTiles, wp_tile(smem));
+      cta_signal(done + 2 * g);
+    } else if (kind == 1) {  // ---- row r of unit g - lagF
+      const uint32_t unit = g - A.lagF;
+      cta_wait(done + 2 * unit, A.F + A.withheld, err);
+      stop = !w_row_task<MODE, false, uint64_t, false, LZ>(P, unit, r, smem, phase);
+      phase ^= 1u;
+      cta_signal(done + 2 * unit + 1);
+    } else {  // ---- column inverse r of unit g - lagI
+      const uint32_t unit = g - A.lagI;
+      cta_wait(done + 2 * unit + 1, A.W, err);
+      w_coli_task<CL, false, uint64_t, false, LZ, kWThreads, kWpMW<CL>>(P, unit, r,
+                                                                        wp_tile(smem));
     }
     // a row task whose copies never completed leaves the barrier's phase
     // unknown: this CTA stops taking tickets (the others finish the queue)
@@ -113,20 +122,6 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<CL>) k_wpersist(KParams P, 
 __host__ __device__ constexpr uint32_t wp_tiles(uint32_t cl) {
   // kW / CT = 4 J with J = R / MW threads per column (MW = 8, or 16 at 2^17)
   return cl == 7 ? 32u : cl > 3 ? 4u << (cl - 3) : 4u;
-}
-
-__device__ __forceinline__ uint32_t wp_find_unit(const uint32_t* __restrict__ pre, uint32_t n,
-                                                 uint32_t x) {
-  // largest u with pre[u] <= x, pre[0] = 0, pre non-decreasing, n >= 1
-  uint32_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (__ldg(pre + mid) <= x)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
 }
 
 template <bool LZ>
@@ -172,9 +167,14 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<7>) k_wuneven(KParams P, Un
       const uint32_t t = atomicAdd(A.ctl, 1u);
       s_ticket = t;
       if (t < total) {
-        const uint32_t* pre = t < A.tf ? A.pre_f : t < A.tf + A.tw ? A.pre_w : A.pre_i;
-        const uint32_t base = t < A.tf ? 0u : t < A.tf + A.tw ? A.tf : A.tf + A.tw;
-        s_unit = wp_find_unit(pre, A.nunits, t - base);
+        const uint32_t sec = t < A.tf ? 0u : t < A.tf + A.tw ? 1u : 2u;
+        const uint32_t* pre = sec == 0 ? A.pre_f : sec == 1 ? A.pre_w : A.pre_i;
+        const uint32_t* blk = sec == 0 ? A.blk_f : sec == 1 ? A.blk_w : A.blk_i;
+        const uint32_t x = t - (sec == 0 ? 0u : sec == 1 ? A.tf : A.tf + A.tw);
+        // the unit holding ticket 32 (x / 32), then forward to x's unit
+        uint32_t u = __ldg(blk + (x >> 5));
+        while (u + 1 < A.nunits && __ldg(pre + u + 1) <= x) ++u;
+        s_unit = u;
       }
     }
     __syncthreads();
@@ -301,8 +301,28 @@ cudaError_t launch_polymul_wpersistent(const KParams& P0, uint32_t* ctl, int gri
   A.I = wp_tiles(cl);
   A.lagF = lagF;
   A.lagI = lagI > lagF ? lagI : lagF + 1;
-  A.ntasks = (P.nunits + A.lagI) * (A.F + A.W + A.I);
   A.withheld = withheld;
+  // segments of groups with the same set of tasks: breakpoints at lagF,
+  // lagI, U, U + lagF (U + lagI ends the last one)
+  const uint32_t U = P.nunits, G = U + A.lagI;
+  uint32_t bp[6] = {0, A.lagF, A.lagI, U, U + A.lagF, G};
+  std::sort(bp, bp + 6);
+  uint32_t t = 0;
+  A.nseg = 0;
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t g0 = bp[k], g1 = bp[k + 1];
+    if (g1 <= g0 || g0 >= G) continue;
+    const uint32_t mask = (g0 < U ? 1u : 0u) | (g0 >= A.lagF && g0 < U + A.lagF ? 2u : 0u) |
+                          (g0 >= A.lagI && g0 < U + A.lagI ? 4u : 0u);
+    const uint32_t gs = ((mask & 1) ? A.F : 0u) + ((mask & 2) ? A.W : 0u) + ((mask & 4) ? A.I : 0u);
+    if (gs == 0) continue;
+    A.seg_g[A.nseg] = g0;
+    A.seg_t[A.nseg] = t;
+    A.seg_mask[A.nseg] = mask;
+    ++A.nseg;
+    t += (g1 - g0) * gs;
+  }
+  A.ntasks = t;
   cudaError_t e = cudaMemsetAsync(ctl, 0, persist_ctl_words(P.nunits) * 4, st);
   if (e != cudaSuccess) return e;
   switch (cl) {

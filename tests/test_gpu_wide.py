@@ -160,7 +160,7 @@ def test_wide_tuning_range():
     plan, *_ = _plan(14, 1)
     assert capi.pm_plan_get_tuning(plan.handle).row_ops == 4
     with pytest.raises(capi.PMError) as e:
-        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=5)
+        capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=6)
     assert e.value.status == -1
 
 
@@ -213,3 +213,37 @@ def test_short_twiddles_times_out_then_recovers(oracle):
     got = to_host(plan.polymul(da, db))
     plan.sync()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("fused", [False, True], ids=["eq2", "alg8"])
+@pytest.mark.parametrize("qbits", [60, 62])
+@pytest.mark.parametrize("log2n", [14, 15, 16, 17])
+def test_wide_tensor_copy_columns(oracle, log2n, qbits, fused):
+    """row_ops 5: the column kernels load their tiles with 2-D tensor copies
+    (and the inverse one stores with one).  Products (distinct operands,
+    aliased output, squares), forward and inverse NTTs: every word against
+    the oracle.  62-bit primes take the classic lazy ranges, 60-bit the
+    wide ones.  32 units avoid the one-launch cluster path at N = 2^14."""
+    from paper_2209_01290_gb300 import Plan, capi
+    import oracle as orc
+    n = 1 << log2n
+    L, P = (2, 16) if log2n <= 15 else (2, 2)
+    qs, psis = capi.pm_find_params(log2n, L, qbits)
+    plan = Plan(n, qs, psis, fused=fused)
+    capi.pm_plan_tune(plan.handle, capi.PM_VARIANT_SPLIT, row_ops=5)
+    a, b = operands(78000 + log2n + qbits, qs, P, n)
+    want = oracle_polymul_batch(oracle, a, b, qs, psis)
+    da, db = to_dev(a), to_dev(b)
+    assert np.array_equal(to_host(plan.polymul(da, db)), want)
+    plan.polymul(da, db, out=db)
+    assert np.array_equal(to_host(db), want)
+    da = to_dev(a)
+    assert np.array_equal(to_host(plan.polymul(da, da)),
+                          oracle_polymul_batch(oracle, a, a, qs, psis))
+    x = to_dev(a[:1])
+    plan.ntt_fwd_(x)
+    for l in range(L):
+        assert np.array_equal(to_host(x)[0, l], orc.ntt_fwd_bo(a[0, l], qs[l], psis[l]))
+    plan.ntt_inv_(x)
+    assert np.array_equal(to_host(x), a[:1])
+    plan.sync()
