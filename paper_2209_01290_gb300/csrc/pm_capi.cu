@@ -916,8 +916,8 @@ pm_status pm_plan_autotune(pm_plan* plan, uint32_t npoly, void* stream, pm_tunin
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 8, 64, 1});
     cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 3, 16, 128, 1});
     if (pm::wpersist_ok(plan->logn) && !(plan->flags & PM_PLAN_HALVING)) {
-      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 2, 16, 4});
-      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 8, 64, 4});
+      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 8, 32, 4});
+      cand.push_back(pm_tuning{PM_VARIANT_PERSISTENT, 4, 32, 64, 4});
     }
   }
   const size_t words = (size_t)npoly * plan->nlimbs << plan->logn;

@@ -104,14 +104,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// One test of the phase; a thread whose phase is not yet complete is
+// suspended in the instruction for up to kBulkSuspendNs (it resumes as soon
+// as the phase completes), so a waiting warp issues a few instructions
+// instead of spinning.
+constexpr uint32_t kBulkSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "n"(kBulkSuspendNs)
       : "memory");
   return done != 0;
 }

@@ -69,6 +69,10 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<CL>) k_wpersist(KParams P, 
   if (threadIdx.x == 0) mbar_init1(w_row_bar<uint64_t>(smem));
   __syncthreads();
   uint32_t phase = 0;
+  // Tickets are taken one at a time: fetching the next one during a task
+  // (as k_wuneven does) was measured slower here -- an unstarted column task
+  // held by a busy CTA delays the rows that wait for it (C3 at lags 8/32:
+  // 104 vs 87 us).
   for (;;) {
     if (threadIdx.x == 0) s_ticket = atomicAdd(A.ctl, 1u);
     __syncthreads();
@@ -158,29 +162,36 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<7>) k_wuneven(KParams P, Un
   __shared__ uint32_t s_ticket, s_unit;
   uint32_t* done = A.ctl + 4;
   int* err = reinterpret_cast<int*>(A.ctl + 1);
-  if (threadIdx.x == 0) mbar_init1(w_row_bar<uint64_t>(smem));
-  __syncthreads();
-  uint32_t phase = 0;
   const uint32_t total = A.tf + A.tw + A.ti;
+  // thread 0: the unit of ticket t (the block table's unit, then a forward
+  // scan of the section's prefix counts)
+  auto unit_of = [&](uint32_t t) {
+    const uint32_t sec = t < A.tf ? 0u : t < A.tf + A.tw ? 1u : 2u;
+    const uint32_t* pre = sec == 0 ? A.pre_f : sec == 1 ? A.pre_w : A.pre_i;
+    const uint32_t* blk = sec == 0 ? A.blk_f : sec == 1 ? A.blk_w : A.blk_i;
+    const uint32_t x = t - (sec == 0 ? 0u : sec == 1 ? A.tf : A.tf + A.tw);
+    uint32_t u = __ldg(blk + (x >> 5));
+    while (u + 1 < A.nunits && __ldg(pre + u + 1) <= x) ++u;
+    return u;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init1(w_row_bar<uint64_t>(smem));
+    const uint32_t t = atomicAdd(A.ctl, 1u);
+    s_ticket = t;
+    s_unit = t < total ? unit_of(t) : 0u;
+  }
+  __syncthreads();
+  uint32_t ticket = s_ticket, unit = s_unit;
+  uint32_t phase = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const uint32_t t = atomicAdd(A.ctl, 1u);
-      s_ticket = t;
-      if (t < total) {
-        const uint32_t sec = t < A.tf ? 0u : t < A.tf + A.tw ? 1u : 2u;
-        const uint32_t* pre = sec == 0 ? A.pre_f : sec == 1 ? A.pre_w : A.pre_i;
-        const uint32_t* blk = sec == 0 ? A.blk_f : sec == 1 ? A.blk_w : A.blk_i;
-        const uint32_t x = t - (sec == 0 ? 0u : sec == 1 ? A.tf : A.tf + A.tw);
-        // the unit holding ticket 32 (x / 32), then forward to x's unit
-        uint32_t u = __ldg(blk + (x >> 5));
-        while (u + 1 < A.nunits && __ldg(pre + u + 1) <= x) ++u;
-        s_unit = u;
-      }
-    }
-    __syncthreads();
-    const uint32_t ticket = s_ticket, unit = s_unit;
-    __syncthreads();
+    __syncthreads();  // everyone has read s_ticket / s_unit
     if (ticket >= total) break;
+    // the next ticket is taken now (its latency overlaps the task) and its
+    // unit looked up after the task.  Holding one unstarted ticket is safe:
+    // every task waits only for smaller tickets, and the smallest unfinished
+    // ticket is always one a CTA is running.  (C4: 23.2 -> 22.8 ms.)
+    uint32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(A.ctl, 1u);
     const uint32_t cl = __ldg(&A.units[unit].logn) - kWLog;
     bool stop = false;
     if (ticket < A.tf) {
@@ -202,7 +213,13 @@ __global__ void __launch_bounds__(kWThreads, kWpCtas<7>) k_wuneven(KParams P, Un
       wu_coli<LZ>(P, cl, unit, r, wp_tile(smem));
     }
     if (stop) break;
+    if (threadIdx.x == 0) {
+      s_ticket = next;
+      s_unit = next < total ? unit_of(next) : 0u;
+    }
     __syncthreads();
+    ticket = s_ticket;
+    unit = s_unit;
   }
 }
 
