@@ -311,8 +311,9 @@ typedef struct pm_server_stats {
     uint64_t arena_peak_bytes, arena_used_bytes;
     /* batches launched while others were still unretired, at most (host view) */
     uint64_t max_inflight;
-    /* the largest number of batches whose device intervals (a timing event
-     * before and after each launch on its slot's stream) overlapped */
+    /* the most batches in flight on the device at one instant (device
+     * intervals: a timing event before and after each launch on its slot's
+     * stream; swept over the last 16 batches at each retirement) */
     uint64_t max_device_overlap;
 } pm_server_stats;
 

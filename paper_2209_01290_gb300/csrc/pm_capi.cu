@@ -1558,7 +1558,7 @@ struct pm_server {
   uint64_t min_rows = 0;      // launch threshold while another batch runs
   pm_server_stats stats{};
   cudaEvent_t t0 = nullptr;  // time origin of the batches' device intervals
-  std::deque<std::pair<float, float>> recent;  // device intervals (ms) of the last batches
+  std::deque<std::pair<float, float>> recent;  // device intervals (ms) of the last 16 batches
   pm_status worker_status = PM_OK;
   char worker_msg[256] = "";
 };
@@ -1597,15 +1597,24 @@ void server_loop(pm_server* S) {
           st = PM_ERR_TIMEOUT;
           cudaMemset(sl.queue->d_ctl + 1, 0, 4);
         }
-        // the batch's device interval; count the recent batches it overlapped
+        // the batch's device interval; the most batches running at one
+        // instant among the last 16 (a sweep over their end points)
         float b0 = 0.f, b1 = 0.f;
         if (cudaEventElapsedTime(&b0, S->t0, sl.start) == cudaSuccess &&
             cudaEventElapsedTime(&b1, S->t0, sl.done) == cudaSuccess) {
-          uint64_t over = 1;
-          for (const auto& iv : S->recent) over += (iv.first < b1 && b0 < iv.second) ? 1 : 0;
-          if (over > S->stats.max_device_overlap) S->stats.max_device_overlap = over;
           S->recent.emplace_back(b0, b1);
-          if (S->recent.size() > 64) S->recent.pop_front();
+          if (S->recent.size() > 16) S->recent.pop_front();
+          std::vector<std::pair<float, int>> ends;
+          for (const auto& iv : S->recent) {
+            ends.emplace_back(iv.first, 1);
+            ends.emplace_back(iv.second, -1);
+          }
+          std::sort(ends.begin(), ends.end());  // at equal times an end (-1) comes first
+          int run = 0;
+          for (const auto& e : ends) {
+            run += e.second;
+            if ((uint64_t)run > S->stats.max_device_overlap) S->stats.max_device_overlap = run;
+          }
         }
       }
       for (uint64_t id : sl.ids) {

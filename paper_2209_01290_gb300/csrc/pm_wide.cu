@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(kWColThreads) k_wcol_inv_tma(KParams P,
 // N = 2^(10+CL), CL = 1..3: one cluster of R = 2^CL CTAs per unit, CTA rank
 // t holding row t in shared memory.  Column steps: CTA t owns columns
 // [t C, (t+1) C), C = 1024 / R.
-template <int MODE, bool HALVE, typename W, int CL>
+// LZ: the wide lazy ranges (64-bit words, q < 2^60, 1/N folded).
+template <int MODE, bool HALVE, typename W, int CL, bool LZ = false>
 __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
   namespace cg = cooperative_groups;
   using Tw = typename WordT<W>::Tw;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
       W x[RR];
 #pragma unroll
       for (int r = 0; r < RR; r++) x[r] = __ldcs(src + (size_t)r * kW);
-      ct_col<RR>(x, twf, K.q, K.two_q);
+      ct_col<RR, W, !LZ>(x, twf, K.q, K.two_q);
       W* row = op == 0 ? sa : sb;
       const int pj = c + (c >> kLatShift<W>);
 #pragma unroll
@@ -296,25 +297,26 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
     __syncthreads();
   }
   if constexpr (MODE == MODE_FWD) {
-    w_fwd<false>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, false);
+    w_fwd<false, LZ>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, false);
 #pragma unroll
     for (int u = 0; u < 4; u++)
-      __stcs(V.c + base + (size_t)t * kW + 4 * th + u, reduce4(va[u], K.q, K.two_q));
+      __stcs(V.c + base + (size_t)t * kW + 4 * th + u, w_reduce_out<LZ>(va[u], K.q, K.two_q));
     return;  // no shared memory of another CTA is touched after the barrier
   } else {
     if constexpr (MODE != MODE_INV) {
-      w_fwd<true>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, kFused);
+      w_fwd<true, LZ>(va, vb, sa, sb, tw_f, th, K.q, K.two_q, kFused);
       if constexpr (kFused) {
-        fused_pair<false>(va[0], va[1], vb[0], vb[1], wf, K);
-        fused_pair<true>(va[2], va[3], vb[2], vb[3], wf, K);
+        fused_pair<false, LZ>(va[0], va[1], vb[0], vb[1], wf, K);
+        fused_pair<true, LZ>(va[2], va[3], vb[2], vb[3], wf, K);
       } else {
 #pragma unroll
         for (int u = 0; u < 4; u++)
           va[u] =
-              mul_barrett_alg4(reduce4(va[u], K.q, K.two_q), reduce4(vb[u], K.q, K.two_q), K);
+              mul_barrett_alg4(w_reduce_out<LZ>(va[u], K.q, K.two_q),
+                               w_reduce_out<LZ>(vb[u], K.q, K.two_q), K);
       }
     }
-    w_inv_passes<HALVE>(va, sa, tw_i, th, K, kFused);
+    w_inv_passes<HALVE, LZ>(va, sa, tw_i, th, K, kFused);
     // the row's lazy result back into its buffer (each thread rewrites the
     // words it read in the last pass), then the inverse column stages
     int pb, blk;
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
       W x[RR];
 #pragma unroll
       for (int r = 0; r < RR; r++) x[r] = cluster.map_shared_rank(sa, r)[pj];
-      gs_col<RR, HALVE>(x, twi, K);
+      gs_col<RR, HALVE, W, LZ>(x, twi, K);
 #pragma unroll
       for (int r = 0; r < RR; r++) __stcs(V.c + base + (size_t)r * kW + c, csub(x[r], K.q));
     }
@@ -491,6 +493,9 @@ cudaError_t clu_cl(const KParams& P, cudaStream_t st) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if constexpr (sizeof(W) == 8 && !H) {
+    if (use_lazy16<W>(P)) return cudaLaunchKernelEx(&cfg, k_wclu<MODE, H, W, CL, true>, P);
+  }
   return cudaLaunchKernelEx(&cfg, k_wclu<MODE, H, W, CL>, P);
 }
 
@@ -588,10 +593,15 @@ cudaError_t ntt_inv_wide_w(const KParams& P, cudaStream_t st) {
 
 template <bool H, typename W, int CL>
 cudaError_t prepare_clu() {
+  constexpr bool kLz = sizeof(W) == 8 && !H;  // the wide-range forms exist too
   const void* fns[] = {(const void*)k_wclu<MODE_POLYMUL, H, W, CL>,
                        (const void*)k_wclu<MODE_POLYMUL_FUSED, H, W, CL>,
                        (const void*)k_wclu<MODE_FWD, H, W, CL>,
-                       (const void*)k_wclu<MODE_INV, H, W, CL>};
+                       (const void*)k_wclu<MODE_INV, H, W, CL>,
+                       (const void*)k_wclu<MODE_POLYMUL, H, W, CL, kLz>,
+                       (const void*)k_wclu<MODE_POLYMUL_FUSED, H, W, CL, kLz>,
+                       (const void*)k_wclu<MODE_FWD, H, W, CL, kLz>,
+                       (const void*)k_wclu<MODE_INV, H, W, CL, kLz>};
   for (const void* f : fns) {
     cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWRowsSmem<W>);
@@ -636,10 +646,15 @@ cudaError_t wide_desc(const KParams& P, cudaStream_t st) {
 // schedulable on this device?  A refusal only leaves g_clu16 false.
 template <bool H, typename W>
 bool prepare_clu16() {
+  constexpr bool kLz = sizeof(W) == 8 && !H;
   const void* fns[] = {(const void*)k_wclu<MODE_POLYMUL, H, W, 4>,
                        (const void*)k_wclu<MODE_POLYMUL_FUSED, H, W, 4>,
                        (const void*)k_wclu<MODE_FWD, H, W, 4>,
-                       (const void*)k_wclu<MODE_INV, H, W, 4>};
+                       (const void*)k_wclu<MODE_INV, H, W, 4>,
+                       (const void*)k_wclu<MODE_POLYMUL, H, W, 4, kLz>,
+                       (const void*)k_wclu<MODE_POLYMUL_FUSED, H, W, 4, kLz>,
+                       (const void*)k_wclu<MODE_FWD, H, W, 4, kLz>,
+                       (const void*)k_wclu<MODE_INV, H, W, 4, kLz>};
   for (const void* f : fns) {
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWRowsSmem<W>) !=
             cudaSuccess ||
