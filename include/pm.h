@@ -367,6 +367,8 @@ pm_status pm_check_reduced(const pm_plan *plan, const uint64_t *d_x, uint32_t np
  *       CTAs, one launch (a thread-block cluster of N/1024 CTAs per unit
  *       exchanging the column stages through distributed shared memory),
  *       otherwise three launches (column stages, rows, column stages);
+ *   5 = 4 with the column stages' tiles moved by 2-D tensor copies (64-bit
+ *       words, 1/N folded; else as 4);
  *   0 = by N, word size and batch size (measured on GB300): 4 for 64-bit
  *       words, except N = 2^12 batches above 64 units; 4 for 32-bit words
  *       in batches of up to 2^20 words; otherwise 3 while the batch has at
