@@ -366,22 +366,31 @@ def run_gpu(args):
     return 0
 
 
-def kernel_sources_sha1() -> str:
-    """Hash of the CUDA sources the kernels are built from, with comments and
-    whitespace removed (so that a comment edit keeps a captured figure)."""
+def kernel_sources_sha1(unit: str = "pm_wide.cu") -> str:
+    """Hash of the translation unit that builds the kernel (`unit` and the
+    headers it includes from the source folder, recursively), with comments
+    and whitespace removed, so that a comment edit, or an edit of another
+    kernel or of host code, keeps a captured figure."""
     import hashlib
     import re
-    h = hashlib.sha1()
     csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2209_01290_gb300",
                         "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f)) as fh:
-                code = fh.read()
-            code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
-            code = re.sub(r"//[^\n]*", "", code)
-            code = re.sub(r"\s+", "", code)
-            h.update(f.encode() + b"\0" + code.encode())
+    seen, todo = set(), [unit]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'#include\s+"([^"]+)"', fh.read())
+    h = hashlib.sha1()
+    for f in sorted(seen):
+        with open(os.path.join(csrc, f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", "", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", "", code)
+        code = re.sub(r"\s+", "", code)
+        h.update(f.encode() + b"\0" + code.encode())
     return h.hexdigest()
 
 

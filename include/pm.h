@@ -318,7 +318,9 @@ typedef struct pm_server_stats {
 } pm_server_stats;
 
 pm_status pm_server_create(pm_server **out, int device, const pm_server_config *cfg);
-/* Drains queued and running requests, then frees everything. */
+/* Drains queued and running requests, then frees everything; a queued
+ * request that cannot fit beside the outputs clients still hold is failed
+ * (PM_ERR_BUDGET) instead of waited for. */
 pm_status pm_server_destroy(pm_server *s);
 /* Queue one request (npoly products of `plan`); PM_ERR_BUDGET if it could
  * never fit.  d_a, d_b must stay valid until the request is done. */

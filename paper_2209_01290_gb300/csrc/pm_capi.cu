@@ -1709,6 +1709,21 @@ void server_loop(pm_server* S) {
           if (ids.size() > S->stats.max_batch) S->stats.max_batch = ids.size();
         }
         progress = true;
+      } else if (S->stop && !running) {
+        // stopping, nothing on the device, and the head request does not fit
+        // beside the outputs clients still hold: it never will, so fail the
+        // rest of the queue instead of waiting for releases
+        for (uint64_t id : S->queued) {
+          Request& r = S->reqs[id];
+          r.state = RQ_DONE;
+          r.status = PM_ERR_BUDGET;
+          r.t_done = now_us();
+        }
+        S->queued.clear();
+        S->queued_rows = 0;
+        snprintf(S->worker_msg, sizeof(S->worker_msg), "server stopped with the arena full");
+        S->cv_done.notify_all();
+        progress = true;
       }
     }
     S->stats.arena_peak_bytes = S->arena.peak;
@@ -1843,11 +1858,16 @@ pm_status pm_server_wait(pm_server* S, uint64_t id, uint32_t timeout_ms, uint64_
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->reqs.find(id);
   if (it == S->reqs.end()) return fail(PM_ERR_ARG, "unknown request %llu", (unsigned long long)id);
+  // find, not operator[]: a request released by another thread meanwhile
+  // must not be re-created as a fresh queued entry
   const bool ready = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
-    return S->reqs[id].state == RQ_DONE;
+    const auto jt = S->reqs.find(id);
+    return jt == S->reqs.end() || jt->second.state == RQ_DONE;
   });
   if (!ready) return fail(PM_ERR_TIMEOUT, "request %llu not done within %u ms", (unsigned long long)id, timeout_ms);
-  Request& r = S->reqs[id];
+  it = S->reqs.find(id);
+  if (it == S->reqs.end()) return fail(PM_ERR_ARG, "request %llu was released", (unsigned long long)id);
+  Request& r = it->second;
   if (r.status != PM_OK) return fail(r.status, "request %llu failed: %s", (unsigned long long)id, S->worker_msg);
   if (d_c_out) *d_c_out = (uint64_t*)(S->arena_base + r.c_off);
   if (latency_us) *latency_us = r.t_done - r.t_submit;

@@ -104,3 +104,28 @@ def test_server_budget_rejects_oversized():
         capi.pm_server_submit(srv, plan.handle, d.data_ptr(), e.data_ptr(), 8)
     assert ex.value.status == -8
     capi.pm_server_destroy(srv)
+
+
+def test_server_stop_with_arena_held():
+    """Destroying a server whose queued request cannot fit beside the
+    outputs the client still holds fails that request instead of waiting
+    for releases that never come: destroy returns promptly."""
+    import time
+    from paper_2209_01290_gb300 import Plan, capi
+    qs, psis = capi.pm_find_params(16, 1, 60)
+    plan = Plan(1 << 16, qs, psis)
+    a, b = operands(81000, qs, 4, 1 << 16)
+    da, db = to_dev(a), to_dev(b)
+    # 8 MiB: each request holds a 2 MiB output (plus 2 MiB of scratch while
+    # it runs); three held outputs leave no room for a fourth request
+    srv = capi.pm_server_create(0, 8 << 20, 0, 1)
+    for _ in range(3):
+        rid = capi.pm_server_submit(srv, plan.handle, da.data_ptr(), db.data_ptr(), 4)
+        capi.pm_server_wait(srv, rid)
+    stuck = capi.pm_server_submit(srv, plan.handle, da.data_ptr(), db.data_ptr(), 4)
+    with pytest.raises(capi.PMError) as ex:
+        capi.pm_server_wait(srv, stuck, timeout_ms=200)
+    assert ex.value.status == -7
+    t0 = time.time()
+    capi.pm_server_destroy(srv)
+    assert time.time() - t0 < 10
