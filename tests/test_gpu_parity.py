@@ -253,13 +253,13 @@ def test_streams_and_large_batch_sampled(torch_cuda, oracle):
 @pytest.mark.slow
 @pytest.mark.parametrize("row_ops", [0, 2], ids=["default", "rows4096"])
 def test_headline_batch_sampled(torch_cuda, oracle, row_ops):
-    """The benchmark's own workload and launch: 1024 products of N=2^16 with
+    """The benchmark's own workload and launch: 4096 products of N=2^16 with
     the largest 60-bit prime in one pm_polymul (default tuning: the
     1024-word split; also the 4096-word split).  Sampled units are checked in
     full against the oracle, sampled coefficients against the definition,
     and every output word is checked to be reduced."""
     from paper_2209_01290_gb300 import inputs
-    log2n, P = 16, 1024
+    log2n, P = 16, 4096
     n = 1 << log2n
     plan, qs, psis = _plan(log2n, 1, variant=(0, row_ops) if row_ops else None)
     da = inputs.uniform_limbs_torch(inputs.seed_for(9), qs, P, n)
