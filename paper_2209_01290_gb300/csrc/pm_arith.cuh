@@ -121,6 +121,22 @@ __device__ __forceinline__ W csub(W x, W m) {
   return (typename WordT<W>::SW)t < 0 ? x : t;
 }
 
+// 64-bit words: the borrow of the subtraction's carry chain as a mask and a
+// bitwise select (lop3: mask ? x : x - m) instead of a compare and selects.
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) {
+  uint32_t lo, hi;
+  asm("{\n\t.reg .u32 b, tl, th;\n\t"
+      "sub.cc.u32 tl, %2, %4;\n\t"
+      "subc.cc.u32 th, %3, %5;\n\t"
+      "subc.u32 b, 0, 0;\n\t"
+      "lop3.b32 %0, tl, %2, b, 0xD8;\n\t"
+      "lop3.b32 %1, th, %3, b, 0xD8;\n\t"
+      "}"
+      : "=r"(lo), "=r"(hi)
+      : "r"((uint32_t)x), "r"((uint32_t)(x >> 32)), "r"((uint32_t)m), "r"((uint32_t)(m >> 32)));
+  return ((uint64_t)hi << 32) | lo;
+}
+
 // Merged-CT butterfly (Algorithm 6 body):
 //   (x, y) <- (x + w y, x - w y) mod q
 // on lazy representatives in [0, 4q).
