@@ -41,6 +41,8 @@ struct KParams {
   uint32_t inject_tx;    // test hook: extra bytes each row CTA's barrier expects (0)
   uint32_t tma_cols;     // 1024-word split, 64-bit words, 1/N folded: the column kernels
                          // load their tiles with 2-D tensor copies (pm_plan_tune row_ops 5)
+  uint32_t pdl;          // launched with a programmatic dependency on the previous kernel
+                         // of the stream: wait (griddepcontrol) before reading its output
 };
 
 // Optional profiling hook: when set, the launcher records ev[k] on the

@@ -64,6 +64,7 @@ namespace {
 template <int MODE, bool HALVE, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWThreads, 4) k_wrows(KParams P) {
   extern __shared__ __align__(16) uint64_t smem_raw[];
+  pdl_trigger();
   const uint32_t cl = P.logn - kWLog;
   const uint32_t unit = blockIdx.x >> cl;
   if (unit >= P.nunits) return;  // whole CTA exits together
@@ -82,6 +83,7 @@ template <int CL, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_fwd(KParams P, int nops) {
   using S = WCol<CL>;
   __shared__ W tile_s[S::kSmemWords];
+  pdl_trigger();
   const uint32_t tile = blockIdx.x % S::kTiles;
   const uint32_t rest = blockIdx.x / S::kTiles;
   const uint32_t op = rest % (uint32_t)nops, unit = rest / (uint32_t)nops;
@@ -94,6 +96,7 @@ template <int CL, bool HALVE, typename W, bool DESC = false, bool LZ = false>
 __global__ void __launch_bounds__(kWColThreads) k_wcol_inv(KParams P) {
   using S = WCol<CL>;
   __shared__ W tile_s[S::kSmemWords];
+  if (P.pdl) pdl_wait();  // c is the row kernel's output
   const uint32_t tile = blockIdx.x % S::kTiles;
   const uint32_t unit = blockIdx.x / S::kTiles;
   if (unit >= P.nunits) return;
@@ -339,6 +342,29 @@ __global__ void __launch_bounds__(kWThreads, 4) k_wclu(KParams P) {
 
 // ------------------------------------------------------------ launchers
 
+// A launch of `k`, with a programmatic dependency on the stream's previous
+// kernel when `pdl` (the kernel then waits in pdl_wait before reading that
+// kernel's output), else an ordinary launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dep(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t st, bool pdl, Args... args) {
+  if (!pdl) {
+    k<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // The wide lazy ranges apply to 64-bit words with every q < 2^60 and the
 // 1/N fold (the host sets P.lazy16 only then).
 template <typename W>
@@ -350,13 +376,15 @@ template <int MODE, typename W>
 cudaError_t wrows(const KParams& P, cudaStream_t st) {
   const size_t blocks = (size_t)P.nunits << (P.logn - kWLog);
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
+  const bool pdl = P.pdl != 0;
   if (use_lazy16<W>(P))
-    k_wrows<MODE, false, W, false, true><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
-  else if (P.halving)
-    k_wrows<MODE, true, W><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
-  else
-    k_wrows<MODE, false, W><<<(unsigned)blocks, kWThreads, kWRowsSmem<W>, st>>>(P);
-  return cudaGetLastError();
+    return launch_dep(k_wrows<MODE, false, W, false, true>, (unsigned)blocks, kWThreads,
+                      kWRowsSmem<W>, st, pdl, P);
+  if (P.halving)
+    return launch_dep(k_wrows<MODE, true, W>, (unsigned)blocks, kWThreads, kWRowsSmem<W>, st, pdl,
+                      P);
+  return launch_dep(k_wrows<MODE, false, W>, (unsigned)blocks, kWThreads, kWRowsSmem<W>, st, pdl,
+                    P);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
@@ -440,13 +468,13 @@ cudaError_t wcol_inv_cl(const KParams& P, cudaStream_t st) {
   }
   const size_t blocks = (size_t)P.nunits * WCol<CL>::kTiles;
   if (blocks > (size_t)INT_MAX) return cudaErrorInvalidConfiguration;
+  const bool pdl = P.pdl != 0;
   if (use_lazy16<W>(P))
-    k_wcol_inv<CL, false, W, false, true><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
-  else if (P.halving)
-    k_wcol_inv<CL, true, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
-  else
-    k_wcol_inv<CL, false, W><<<(unsigned)blocks, kWColThreads, 0, st>>>(P);
-  return cudaGetLastError();
+    return launch_dep(k_wcol_inv<CL, false, W, false, true>, (unsigned)blocks, kWColThreads, 0,
+                      st, pdl, P);
+  if (P.halving)
+    return launch_dep(k_wcol_inv<CL, true, W>, (unsigned)blocks, kWColThreads, 0, st, pdl, P);
+  return launch_dep(k_wcol_inv<CL, false, W>, (unsigned)blocks, kWColThreads, 0, st, pdl, P);
 }
 
 template <typename W>
@@ -562,9 +590,11 @@ cudaError_t polymul_wide_w(const KParams& P0, cudaStream_t st, const PhaseEvents
   }
   e = wcol_fwd<W>(P, nops, st);
   if (e == cudaSuccess) e = mark(pe, 1, st);
-  if (e == cudaSuccess) e = prows(P);
+  KParams Q = P;
+  Q.pdl = 1;  // rows after the forward columns, inverse columns after the rows
+  if (e == cudaSuccess) e = prows(Q);
   if (e == cudaSuccess) e = mark(pe, 2, st);
-  if (e == cudaSuccess) e = wcol_inv<W>(P, st);
+  if (e == cudaSuccess) e = wcol_inv<W>(Q, st);
   if (e == cudaSuccess) e = mark(pe, 3, st);
   return e;
 }
@@ -578,6 +608,7 @@ cudaError_t ntt_fwd_wide_w(const KParams& P0, cudaStream_t st) {
     P.a = P.c;  // in place: the column stages read and write x
     cudaError_t e = wcol_fwd<W>(P, 1, st);
     if (e != cudaSuccess) return e;
+    P.pdl = 1;
   }
   return wrows<MODE_FWD, W>(P, st);
 }
@@ -588,7 +619,9 @@ cudaError_t ntt_inv_wide_w(const KParams& P, cudaStream_t st) {
   if (clustered(P.logn, P.nunits)) return clu<MODE_INV, W>(P, st);
   cudaError_t e = wrows<MODE_INV, W>(P, st);
   if (e != cudaSuccess || P.logn == kWLog) return e;
-  return wcol_inv<W>(P, st);
+  KParams Q = P;
+  Q.pdl = 1;
+  return wcol_inv<W>(Q, st);
 }
 
 template <bool H, typename W, int CL>

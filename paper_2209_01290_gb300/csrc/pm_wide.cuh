@@ -76,6 +76,17 @@ __device__ __forceinline__ void w_stage_tw(typename WordT<W>::Tw* dst,
   }
 }
 
+// ------------------------------------------- programmatic dependent launch
+// The split's second and third kernels are launched with a programmatic
+// dependency on the one before: they may start while it finishes, do what
+// does not depend on it (the row kernel stages its twiddles), and wait here
+// for its completion and memory before reading its output.  The first two
+// kernels let their dependents start once all their CTAs are running.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------ bulk copies (TMA)
 // 64-bit words: the same slices copied by the tensor-memory-accelerator's
 // 1-D bulk copies, ten per table (slice r is 2^r x 16 bytes, 16-byte aligned
@@ -415,6 +426,7 @@ __device__ __forceinline__ bool w_row_task(const KParams& P, uint32_t unit, uint
     if constexpr (MODE != MODE_FWD) w_stage_tw<W>(tw_i, twi, logn, t, th);
     cp_async_commit();
   }
+  if (P.pdl) pdl_wait();  // the rows are the previous kernel's output
   W va[4], vb[4];
   Tw wf{};
   if constexpr (MODE == MODE_INV) {
